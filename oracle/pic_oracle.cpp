@@ -204,22 +204,20 @@ void add_at(const or_grid& g, T* F, long long i, long long j, long long k, T v) 
     F[lin(g, ijk[0], ijk[1], ijk[2])] += v;
 }
 
-// Current of one straight segment that stays inside cell `cell`; a and b are
-// its end points relative to the cell corner, in cells.  For the x component,
-// the charge-conserving current on the four x-edges (i+1/2, j+s1, k+s2) is the
-// line integral of the CIC weights of the other two coordinates along the
-// segment: dx * [W_y(s1) W_z(s2) + sigma dy dz / 12], with W(0) = 1 - mid,
-// W(1) = mid and sigma = +1 when s1 == s2, -1 otherwise.  Y and Z follow by
-// cycling the axes.  qfac[c] = q w / (dt * product of the two other cell
-// sizes) turns the displacement (in cells) into a current density.
+// Current of one straight segment that stays inside cell `cell`; a is its
+// start point relative to the cell corner and d its displacement, in cells.
+// For the x component, the charge-conserving current on the four x-edges
+// (i+1/2, j+s1, k+s2) is the line integral of the CIC weights of the other two
+// coordinates along the segment: dx * [W_y(s1) W_z(s2) + sigma dy dz / 12],
+// with W(0) = 1 - mid, W(1) = mid, mid = a + d/2, and sigma = +1 when s1 == s2,
+// -1 otherwise.  Y and Z follow by cycling the axes.  qfac[c] = q w / (dt *
+// product of the two other cell sizes) turns the displacement (in cells) into
+// a current density.
 template <class T>
-void deposit_segment(const or_grid& g, T* J[3], const long long cell[3], const T a[3], const T b[3],
+void deposit_segment(const or_grid& g, T* J[3], const long long cell[3], const T a[3], const T d[3],
                      const T qfac[3]) {
-    T d[3], m[3];
-    for (int e = 0; e < 3; ++e) {
-        d[e] = b[e] - a[e];
-        m[e] = T(0.5) * (a[e] + b[e]);
-    }
+    T m[3];
+    for (int e = 0; e < 3; ++e) m[e] = a[e] + T(0.5) * d[e];
     for (int c = 0; c < 3; ++c) {
         int p = (c + 1) % 3, r = (c + 2) % 3;  // the two transverse axes
         for (int s1 = 0; s1 < 2; ++s1) {
@@ -237,19 +235,20 @@ void deposit_segment(const or_grid& g, T* J[3], const long long cell[3], const T
     }
 }
 
-// Villasenor-Buneman deposition (Sec. 3) of the straight move xi0 -> xi1
-// (positions in cells, xi1 not wrapped): the move is cut at every cell face it
-// crosses (at most one face per axis, since a particle moves less than a cell
-// per step), the pieces are taken in order of the crossing parameter, and each
-// piece deposits the current of a segment inside one cell.
+// Villasenor-Buneman deposition (Sec. 3) of the straight move that starts at
+// xi0 with displacement d (positions in cells, not wrapped): the move is cut
+// at every cell face it crosses (at most one face per axis, since a particle
+// moves less than a cell per step), the pieces are taken in order of the
+// crossing parameter t in [0,1], and each piece -- start xi0 + t_a d,
+// displacement (t_b - t_a) d -- deposits the current of a segment inside the
+// cell that holds its midpoint.  The displacement enters as given, never as a
+// difference of two rounded positions.
 template <class T>
-void deposit_vb(const or_grid& g, T* J[3], const T xi0[3], const T xi1[3], const T qfac[3]) {
-    T d[3];
-    for (int a = 0; a < 3; ++a) d[a] = xi1[a] - xi0[a];
+void deposit_vb(const or_grid& g, T* J[3], const T xi0[3], const T d[3], const T qfac[3]) {
     std::vector<T> ts;
     ts.push_back(T(0.0));
     for (int a = 0; a < 3; ++a) {
-        double c0 = std::floor(val(xi0[a])), c1 = std::floor(val(xi1[a]));
+        double c0 = std::floor(val(xi0[a])), c1 = std::floor(val(xi0[a] + d[a]));
         if (c0 != c1) {
             double face = std::max(c0, c1);
             ts.push_back((T(face) - xi0[a]) / d[a]);
@@ -258,16 +257,15 @@ void deposit_vb(const or_grid& g, T* J[3], const T xi0[3], const T xi1[3], const
     ts.push_back(T(1.0));
     std::sort(ts.begin(), ts.end(), [](const T& p, const T& q) { return val(p) < val(q); });
     for (size_t s = 0; s + 1 < ts.size(); ++s) {
-        T pa[3], pb[3], a[3], b[3];
+        T pa[3], ds[3], a[3];
         long long cell[3];
         for (int e = 0; e < 3; ++e) {
             pa[e] = xi0[e] + ts[s] * d[e];
-            pb[e] = xi0[e] + ts[s + 1] * d[e];
-            cell[e] = (long long)std::floor(0.5 * (val(pa[e]) + val(pb[e])));
+            ds[e] = (ts[s + 1] - ts[s]) * d[e];
+            cell[e] = (long long)std::floor(val(pa[e]) + 0.5 * val(ds[e]));
             a[e] = pa[e] - double(cell[e]);
-            b[e] = pb[e] - double(cell[e]);
         }
-        deposit_segment(g, J, cell, a, b, qfac);
+        deposit_segment(g, J, cell, a, ds, qfac);
     }
 }
 
@@ -376,10 +374,11 @@ void push_and_deposit(const or_grid& g, T* const E[3], T* const B[3], T* J[3], S
         gather_one(g, E, B, xi0, Ep, Bp);
         boris(u, Ep, Bp, sp.q, sp.m, g.dt);
         T gam = sqrt(T(1.0) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        T xn[3], xi1[3];
+        T xn[3], dcell[3];
         for (int a = 0; a < 3; ++a) {
-            xn[a] = *X[a] + g.dt * u[a] / gam;
-            xi1[a] = xn[a] / g.d[a];
+            T disp = g.dt * u[a] / gam;  // x^{n+1} - x^n
+            xn[a] = *X[a] + disp;
+            dcell[a] = disp / g.d[a];
         }
         if (sp.q != 0.0) {
             T qfac[3];
@@ -387,7 +386,7 @@ void push_and_deposit(const or_grid& g, T* const E[3], T* const B[3], T* J[3], S
                 int p1 = (c + 1) % 3, p2 = (c + 2) % 3;
                 qfac[c] = sp.q * sp.w[p] / (g.dt * g.d[p1] * g.d[p2]);
             }
-            deposit_vb(g, J, xi0, xi1, qfac);
+            deposit_vb(g, J, xi0, dcell, qfac);
         }
         bool leaves = false;
         for (int a = 0; a < 3; ++a) {
@@ -482,14 +481,14 @@ void or_deposit(const or_grid* g, double* const* J, int64_t n, const double* x0,
                 const double* w, double q) {
     double* Jp[3] = {J[0], J[1], J[2]};
     for (int64_t p = 0; p < n; ++p) {
-        double xi0[3], xi1[3], qfac[3];
+        double xi0[3], dc[3], qfac[3];
         for (int a = 0; a < 3; ++a) {
             xi0[a] = x0[a * n + p] / g->d[a];
-            xi1[a] = x1[a * n + p] / g->d[a];
+            dc[a] = (x1[a * n + p] - x0[a * n + p]) / g->d[a];
         }
         for (int c = 0; c < 3; ++c)
             qfac[c] = q * w[p] / (g->dt * g->d[(c + 1) % 3] * g->d[(c + 2) % 3]);
-        deposit_vb(*g, Jp, xi0, xi1, qfac);
+        deposit_vb(*g, Jp, xi0, dc, qfac);
     }
 }
 

@@ -30,7 +30,9 @@ MUTATIONS = [
      "(at(g, E[2], i + 1, j, k) - at(g, E[2], i, j, k)) * ry;"),
     ("Ampere current sign", "nE[1][o] = E[1][o] + dt * (cy - J[1][o]);", "nE[1][o] = E[1][o] + dt * (cy + J[1][o]);"),
     ("gather weight", "T wx = bx ? f[0] : T(1.0) - f[0];", "T wx = bx ? T(1.0) - f[0] : f[0];"),
-    ("move uses u not v", "xn[a] = *X[a] + g.dt * u[a] / gam;", "xn[a] = *X[a] + g.dt * u[a];"),
+    ("move uses u not v", "T disp = g.dt * u[a] / gam;", "T disp = g.dt * u[a];"),
+    ("segment midpoint", "for (int e = 0; e < 3; ++e) m[e] = a[e] + T(0.5) * d[e];",
+     "for (int e = 0; e < 3; ++e) m[e] = a[e] + d[e];"),
     ("kinetic energy rest mass", "s += sp.w[p] * (gam - T(1.0));", "s += sp.w[p] * gam;"),
 ]
 
