@@ -1,0 +1,208 @@
+/*
+ * pic.h -- C ABI of the GB300 particle-in-cell hot path (libpicgb.so).
+ *
+ * The library advances the particle-in-cell cycle that arXiv:1608.01009
+ * (Surmin et al., "Co-design of a particle-in-cell plasma simulation code for
+ * Intel Xeon Phi: a first look at Knights Landing") sets out in Sec. 2 and
+ * Sec. 3: Maxwell's equations integrated on a grid, the field interpolated to
+ * each macro-particle with the cloud-in-cell form factor, the relativistic
+ * equations of motion, and the Villasenor-Buneman charge-conserving current
+ * deposition, in double precision.  The paper names neither pusher nor field
+ * solver; this library uses the relativistic Boris pusher and the Yee FDTD
+ * scheme (staggering below), with B split into two half steps so that E and B
+ * are both known at integer time levels when the particles are pushed.
+ *
+ * Units are normalised to a reference frequency w_r: time 1/w_r, length
+ * c/w_r, momentum u = gamma v / c, fields m_e c w_r / e, current e n_r c.
+ * Maxwell: dE/dt = curl B - J, dB/dt = -curl E.  Motion: du/dt = (q/m)(E +
+ * u x B / gamma), dx/dt = u / gamma.  Weight w = real particles per
+ * macro-particle in these units (density x cell volume / particles per cell).
+ *
+ * Yee staggering (cell (i,j,k) has its corner node at (i dx, j dy, k dz)):
+ *   Ex (i+1/2, j, k)   Ey (i, j+1/2, k)   Ez (i, j, k+1/2)   (J the same)
+ *   Bx (i, j+1/2, k+1/2)   By (i+1/2, j, k+1/2)   Bz (i+1/2, j+1/2, k)
+ * Field arrays at this ABI are unpadded, nx*ny*nz doubles per component, x
+ * fastest: element (i,j,k) at index i + nx*(j + ny*k).
+ *
+ * One step (state x^n, u^{n-1/2}, E^n, B^n):
+ *   gather E^n, B^n at x^n; Boris u^{n-1/2} -> u^{n+1/2};
+ *   x^{n+1} = x^n + dt u^{n+1/2} / gamma; deposit J^{n+1/2} from x^n -> x^{n+1};
+ *   B^{n+1/2} = B^n - dt/2 curl E^n; E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2});
+ *   B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1}.
+ *
+ * Conventions of every call:
+ *   - returns PIC_OK (0) or a negative pic_status; no exception crosses the
+ *     ABI and no kernel traps; pic_last_error() gives a message;
+ *   - "_dev" variants take device pointers (e.g. from torch tensors) and work
+ *     asynchronously on the context's stream; the others take host pointers
+ *     and return once the copy is complete;
+ *   - the caller owns every buffer it passes; the library owns its context
+ *     and all device state, released by pic_destroy();
+ *   - one context is used from one host thread at a time.
+ */
+#ifndef PICGB_PIC_H
+#define PICGB_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = -1,          /* invalid argument or descriptor */
+    PIC_ERR_CFL = -2,          /* time step violates the Courant limit or the sort interval */
+    PIC_ERR_OOM = -3,          /* device allocation failed */
+    PIC_ERR_BIN_OVERFLOW = -4, /* a particle left its supercell's halo slack between sorts */
+    PIC_ERR_NAN = -5,          /* a non-finite value reached the energy diagnostics */
+    PIC_ERR_CUDA = -6,         /* a CUDA runtime call failed */
+    PIC_ERR_STATE = -7,        /* call not valid in the current state */
+    PIC_ERR_TIMEOUT = -8       /* a bounded wait inside a kernel expired */
+} pic_status;
+
+enum { PIC_BC_PERIODIC = 0, PIC_BC_ABSORBING = 1 };
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };
+
+/* Grid and run descriptor.
+ *   n[3]          cells per axis; each a multiple of `supercell`, 4..1024
+ *   d[3]          cell sizes (c/w_r)
+ *   dt            time step (1/w_r); needs dt * sqrt(sum 1/d^2) < 1 (Courant)
+ *   bc[3]         PIC_BC_PERIODIC or PIC_BC_ABSORBING per axis.  Along an
+ *                 absorbing axis the field is zero outside the domain, current
+ *                 deposited outside it is dropped, particles leaving it are
+ *                 deactivated, and after each field sub-update E and B inside a
+ *                 layer of `absorb_cells` cells are multiplied by
+ *                 1 - absorb_sigma ((L - dist)/L)^2 (dist = distance in cells of
+ *                 the component's lattice point from the nearer boundary).
+ *   precision     PIC_FP64: particles, interpolation, push and shared-memory
+ *                 current sums in FP64.  PIC_MIXED: cell-relative FP32 particle
+ *                 offsets, FP32 momenta, FP32 interpolation from an FP32 copy of
+ *                 the fields and FP32 shared-memory current sums; global current,
+ *                 fields and energy diagnostics stay FP64.
+ *   supercell     S, cells per supercell edge: 4 or 8 (2 also for PIC_FP64)
+ *   sort_interval K, steps between supercell re-sorts; 0 = the largest allowed,
+ *                 K * max_a(dt / d_a) < 1 (a particle moves less than one cell
+ *                 per step along each axis, and the supercell tiles carry one
+ *                 cell of slack)
+ *   device        CUDA device ordinal
+ *   stream        cudaStream_t the context works on (NULL = legacy default)
+ */
+typedef struct {
+    int32_t n[3];
+    double d[3];
+    double dt;
+    int32_t bc[3];
+    int32_t absorb_cells;
+    double absorb_sigma;
+    int32_t precision;
+    int32_t supercell;
+    int32_t sort_interval;
+    int32_t device;
+    void* stream;
+} pic_grid_desc;
+
+/* Species: charge q and mass m in units of e and m_e (electrons: -1, 1). */
+typedef struct {
+    double q;
+    double m;
+} pic_species_desc;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Create a context: validates `g` (PIC_ERR_ARG, PIC_ERR_CFL) before touching
+ * the GPU, then allocates the ghost-padded FP64 E, B, J grids (and the FP32
+ * field copy in mixed mode), all zero.  *out receives the context. */
+PIC_API int pic_create(const pic_grid_desc* g, pic_ctx** out);
+
+/* Wait for the context's stream and release everything it owns. */
+PIC_API int pic_destroy(pic_ctx* ctx);
+
+/* Message of the last error of this context ("" if none); valid until the
+ * next call on the context. */
+PIC_API const char* pic_last_error(const pic_ctx* ctx);
+
+/* Add a species of n macro-particles (Sec. 2: the plasma is represented by
+ * macro-particles).  x,y,z are physical positions inside the domain,
+ * ux,uy,uz the momenta u^{-1/2}, w the weights; each array has n doubles.
+ * Particles are given ids 0..n-1 in input order, binned by supercell and
+ * stored in the library (FP64 or FP32 per `precision`).  *species_id receives
+ * the species index.  Host variant: copies and returns when done. */
+PIC_API int pic_add_species(pic_ctx* ctx, const pic_species_desc* s, int64_t n, const double* x, const double* y,
+                    const double* z, const double* ux, const double* uy, const double* uz, const double* w,
+                    int* species_id);
+PIC_API int pic_add_species_dev(pic_ctx* ctx, const pic_species_desc* s, int64_t n, const double* x,
+                        const double* y, const double* z, const double* ux, const double* uy,
+                        const double* uz, const double* w, int* species_id);
+
+/* Replace all particles of an existing species (same layout as
+ * pic_add_species; ids restart at 0).  Used to load a new state. */
+PIC_API int pic_set_particles(pic_ctx* ctx, int species, int64_t n, const double* x, const double* y, const double* z,
+                      const double* ux, const double* uy, const double* uz, const double* w);
+PIC_API int pic_set_particles_dev(pic_ctx* ctx, int species, int64_t n, const double* x, const double* y,
+                          const double* z, const double* ux, const double* uy, const double* uz,
+                          const double* w);
+
+/* Number of active particles of a species (synchronises the stream). */
+PIC_API int pic_count_particles(pic_ctx* ctx, int species, int64_t* n);
+
+/* Copy out the active particles of a species: ids, physical positions
+ * (wrapped into the domain on periodic axes), momenta and weights, FP64.
+ * Order is the library's internal (binned) order; match by id.  `cap` is
+ * the length of the caller's arrays; *n receives the count written
+ * (PIC_ERR_ARG if cap is too small).  Synchronises the stream. */
+PIC_API int pic_get_particles(pic_ctx* ctx, int species, int64_t cap, int64_t* n, int64_t* id, double* x, double* y,
+                      double* z, double* ux, double* uy, double* uz, double* w);
+PIC_API int pic_get_particles_dev(pic_ctx* ctx, int species, int64_t cap, int64_t* n, int64_t* id, double* x,
+                          double* y, double* z, double* ux, double* uy, double* uz, double* w);
+
+/* Set / get E and B (unpadded layout above; E[c], B[c] one array per
+ * component).  Setting refreshes the periodic ghost layers and the FP32
+ * copy.  Getting returns E^n, B^n of the current state. */
+PIC_API int pic_set_fields(pic_ctx* ctx, const double* const E[3], const double* const B[3]);
+PIC_API int pic_set_fields_dev(pic_ctx* ctx, const double* const E[3], const double* const B[3]);
+PIC_API int pic_get_fields(pic_ctx* ctx, double* const E[3], double* const B[3]);
+PIC_API int pic_get_fields_dev(pic_ctx* ctx, double* const E[3], double* const B[3]);
+
+/* The current density J^{n+1/2} deposited by the last step (periodic images
+ * folded onto their owners), same layout as E. */
+PIC_API int pic_get_current(pic_ctx* ctx, double* const J[3]);
+PIC_API int pic_get_current_dev(pic_ctx* ctx, double* const J[3]);
+
+/* Advance nsteps whole steps (the order above), asynchronously on the
+ * stream.  Every `sort_interval` steps the particles are re-binned by
+ * supercell (an on-device counting sort).  Device-side faults are recorded in
+ * a sticky flag that pic_sync() returns. */
+PIC_API int pic_step(pic_ctx* ctx, int nsteps);
+
+/* Wait for the stream; return the sticky device status (PIC_OK,
+ * PIC_ERR_BIN_OVERFLOW, PIC_ERR_TIMEOUT, PIC_ERR_NAN) or PIC_ERR_CUDA. */
+PIC_API int pic_sync(pic_ctx* ctx);
+
+/* Energy of the current state (synchronises): field energy
+ * W_F = 1/2 dV sum (E^2 + B^2) and kinetic energy W_K = sum m w (gamma - 1)
+ * over active particles, gamma from the stored u^{n-1/2}; FP64. */
+PIC_API int pic_energy(pic_ctx* ctx, double* wf, double* wk);
+
+/* Turn per-stage CUDA-event timing on (1) or off (0, the default), and read
+ * the accumulated milliseconds: out[0] particle push + current deposition
+ * (one fused kernel per species), out[1] field solver, out[2] supercell sort,
+ * out[3] diagnostics.  pic_stage_times synchronises. */
+PIC_API int pic_enable_timing(pic_ctx* ctx, int on);
+PIC_API int pic_stage_times(pic_ctx* ctx, double out[4]);
+
+/* Kernels this context has launched since creation (or the last reset). */
+PIC_API int pic_launch_count(pic_ctx* ctx, int64_t* n, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICGB_PIC_H */

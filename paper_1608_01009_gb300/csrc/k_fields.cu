@@ -1,0 +1,226 @@
+// Yee FDTD field update (the Maxwell stage of arXiv:1608.01009 Sec. 2, which
+// the paper times as "Other"), one thread per cell, x fastest (coalesced).
+//
+//   k_fdtd_b : B <- B - (dt/2) curl E   (forward differences of E)
+//   k_fdtd_e : E <- E + dt (curl B - J) (backward differences of B); folds the
+//              ghost images of J onto their owner, records the folded J and
+//              zeroes every J entry it read, ready for the next deposit
+// Each kernel writes its result into the cell's periodic ghost images too, so
+// the next stencil and the next TMA field tile read valid ghosts with no
+// separate exchange pass.  The second B half step also refreshes the FP32
+// field copy (mixed mode) and writes per-block field-energy partial sums.
+// Along an absorbing axis the ghosts stay zero (no field outside the domain)
+// and each updated component is damped inside the layer.
+#include "pic_internal.cuh"
+
+namespace picgb {
+
+// Image list of domain index i along an axis: the cell itself plus, on a
+// periodic axis, the ghost copy at i+n (i < PAD) or i-n (i >= n-PAD).  On an
+// absorbing axis the ghosts i-PAD (i < PAD) / i+PAD (i >= n-PAD) are listed
+// with fold = false, so the J fold zeroes them without adding them.
+struct Img {
+    int idx[2];
+    bool fold[2];
+    int cnt;
+};
+
+__device__ __forceinline__ Img images(int i, int n, int bc) {
+    Img m;
+    m.idx[0] = i;
+    m.fold[0] = true;
+    m.cnt = 1;
+    if (i < PAD) {
+        m.idx[1] = bc == 0 ? i + n : i - PAD;
+        m.fold[1] = bc == 0;
+        m.cnt = 2;
+    } else if (i >= n - PAD) {
+        m.idx[1] = bc == 0 ? i - n : i + PAD;
+        m.fold[1] = bc == 0;
+        m.cnt = 2;
+    }
+    return m;
+}
+
+// Damping of the absorbing layer at lattice coordinate p (cells) along an axis of n cells.
+__device__ __forceinline__ double damp1(const GridDev& g, double p, int n) {
+    double dist = fmin(p, (double)n - p);
+    double L = (double)g.absorb_cells;
+    if (g.absorb_cells <= 0 || dist >= L) return 1.0;
+    double r = (L - dist) / L;
+    return 1.0 - g.absorb_sigma * r * r;
+}
+
+// Product of the layer factors for component `comp` at cell (i,j,k); stagB
+// selects the B staggering.
+__device__ __forceinline__ double damping(const GridDev& g, int comp, bool magnetic, int i, int j, int k) {
+    double f = 1.0;
+    int ijk[3] = {i, j, k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (g.bc[a] == 0) continue;
+        double off = magnetic ? (comp == a ? 0.0 : 0.5) : (comp == a ? 0.5 : 0.0);
+        f *= damp1(g, ijk[a] + off, g.n[a]);
+    }
+    return f;
+}
+
+__device__ __forceinline__ bool any_absorbing(const GridDev& g) { return (g.bc[0] | g.bc[1] | g.bc[2]) != 0; }
+
+// Store v at the cell and at its periodic ghost images (absorbing ghosts stay 0).
+template <class R>
+__device__ __forceinline__ void store_images(R* A, const GridDev& g, const Img& ix, const Img& iy, const Img& iz,
+                                             R v) {
+    for (int c = 0; c < iz.cnt; ++c) {
+        if (!iz.fold[c]) continue;
+        for (int b = 0; b < iy.cnt; ++b) {
+            if (!iy.fold[b]) continue;
+            for (int a = 0; a < ix.cnt; ++a) {
+                if (!ix.fold[a]) continue;
+                A[pidx(g, ix.idx[a], iy.idx[b], iz.idx[c])] = v;
+            }
+        }
+    }
+}
+
+constexpr int FDTD_NT = 256;
+
+__global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, GridDev g, double h, int last,
+                                                    float* __restrict__ EB32, double* __restrict__ wf_part) {
+    __shared__ double red[FDTD_NT / 32];
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
+    double e2 = 0.0;
+    if (t < ncell) {
+        const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long o = pidx(g, i, j, k);
+        const long long sy = g.np[0], sz = (long long)g.np[0] * g.np[1];
+        const double* Ex = EB;
+        const double* Ey = EB + g.P;
+        const double* Ez = EB + 2 * g.P;
+        double* B = EB + 3 * g.P;
+        const double rx = 1.0 / g.d[0], ry = 1.0 / g.d[1], rz = 1.0 / g.d[2];
+        const double ex = Ex[o], ey = Ey[o], ez = Ez[o];
+        const double cx = (Ez[o + sy] - ez) * ry - (Ey[o + sz] - ey) * rz;
+        const double cy = (Ex[o + sz] - ex) * rz - (Ez[o + 1] - ez) * rx;
+        const double cz = (Ey[o + 1] - ey) * rx - (Ex[o + sy] - ex) * ry;
+        double b[3] = {B[o] - h * cx, B[g.P + o] - h * cy, B[2 * g.P + o] - h * cz};
+        if (any_absorbing(g))
+            for (int c = 0; c < 3; ++c) b[c] *= damping(g, c, true, i, j, k);
+        const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
+        for (int c = 0; c < 3; ++c) store_images(B + c * g.P, g, ix, iy, iz, b[c]);
+        if (last) {
+            if (EB32) {
+                const double e[3] = {ex, ey, ez};
+                for (int c = 0; c < 3; ++c) {
+                    store_images(EB32 + c * g.P, g, ix, iy, iz, (float)e[c]);
+                    store_images(EB32 + (3 + c) * g.P, g, ix, iy, iz, (float)b[c]);
+                }
+            }
+            e2 = ex * ex + ey * ey + ez * ez + b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        }
+    }
+    if (last) {
+        const double s = block_sum<FDTD_NT>(e2, red);
+        if (threadIdx.x == 0) wf_part[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(FDTD_NT) k_fdtd_e(double* __restrict__ EB, double* __restrict__ J,
+                                                    double* __restrict__ Jlast, GridDev g) {
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
+    if (t >= ncell) return;
+    const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    const long long o = pidx(g, i, j, k);
+    const long long sy = g.np[0], sz = (long long)g.np[0] * g.np[1];
+    const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
+    // fold J: sum the cell and its periodic images, zero everything read
+    double jc[3] = {0.0, 0.0, 0.0};
+    for (int c3 = 0; c3 < iz.cnt; ++c3)
+        for (int b3 = 0; b3 < iy.cnt; ++b3)
+            for (int a3 = 0; a3 < ix.cnt; ++a3) {
+                const long long q = pidx(g, ix.idx[a3], iy.idx[b3], iz.idx[c3]);
+                const bool fold = ix.fold[a3] && iy.fold[b3] && iz.fold[c3];
+                for (int c = 0; c < 3; ++c) {
+                    if (fold) jc[c] += J[c * g.P + q];
+                    J[c * g.P + q] = 0.0;
+                }
+            }
+    for (int c = 0; c < 3; ++c) Jlast[c * ncell + t] = jc[c];
+    const double* Bx = EB + 3 * g.P;
+    const double* By = EB + 4 * g.P;
+    const double* Bz = EB + 5 * g.P;
+    const double rx = 1.0 / g.d[0], ry = 1.0 / g.d[1], rz = 1.0 / g.d[2];
+    const double bx = Bx[o], by = By[o], bz = Bz[o];
+    const double cx = (bz - Bz[o - sy]) * ry - (by - By[o - sz]) * rz;
+    const double cy = (bx - Bx[o - sz]) * rz - (bz - Bz[o - 1]) * rx;
+    const double cz = (by - By[o - 1]) * rx - (bx - Bx[o - sy]) * ry;
+    double e[3] = {EB[o] + g.dt * (cx - jc[0]), EB[g.P + o] + g.dt * (cy - jc[1]),
+                   EB[2 * g.P + o] + g.dt * (cz - jc[2])};
+    if (any_absorbing(g))
+        for (int c = 0; c < 3; ++c) e[c] *= damping(g, c, false, i, j, k);
+    for (int c = 0; c < 3; ++c) store_images(EB + c * g.P, g, ix, iy, iz, e[c]);
+}
+
+// Refresh ghosts (and the FP32 copy) from the domain values after E/B are set.
+__global__ void __launch_bounds__(FDTD_NT) k_refresh(double* __restrict__ EB, GridDev g, float* __restrict__ EB32) {
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
+    if (t >= ncell) return;
+    const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    const long long o = pidx(g, i, j, k);
+    const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
+    for (int c = 0; c < 6; ++c) {
+        const double v = EB[c * g.P + o];
+        store_images(EB + c * g.P, g, ix, iy, iz, v);
+        if (EB32) store_images(EB32 + c * g.P, g, ix, iy, iz, (float)v);
+    }
+}
+
+// Field-energy partial sums of the current state (sum of E^2 + B^2 per block).
+__global__ void __launch_bounds__(FDTD_NT) k_field_energy(const double* __restrict__ EB, GridDev g,
+                                                          double* __restrict__ wf_part) {
+    __shared__ double red[FDTD_NT / 32];
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
+    double e2 = 0.0;
+    if (t < ncell) {
+        const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long o = pidx(g, i, j, k);
+        for (int c = 0; c < 6; ++c) {
+            const double v = EB[c * g.P + o];
+            e2 += v * v;
+        }
+    }
+    const double s = block_sum<FDTD_NT>(e2, red);
+    if (threadIdx.x == 0) wf_part[blockIdx.x] = s;
+}
+
+int fdtd_blocks(const GridDev& g) {
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    return (int)((ncell + FDTD_NT - 1) / FDTD_NT);
+}
+
+cudaError_t fdtd_b_launch(cudaStream_t st, double* EB, const GridDev& g, double h, int last, float* EB32,
+                          double* wf_part) {
+    k_fdtd_b<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, g, h, last, EB32, wf_part);
+    return cudaGetLastError();
+}
+
+cudaError_t fdtd_e_launch(cudaStream_t st, double* EB, double* J, double* Jlast, const GridDev& g) {
+    k_fdtd_e<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, J, Jlast, g);
+    return cudaGetLastError();
+}
+
+cudaError_t refresh_launch(cudaStream_t st, double* EB, const GridDev& g, float* EB32) {
+    k_refresh<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, g, EB32);
+    return cudaGetLastError();
+}
+
+cudaError_t field_energy_launch(cudaStream_t st, const double* EB, const GridDev& g, double* wf_part) {
+    k_field_energy<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, g, wf_part);
+    return cudaGetLastError();
+}
+
+}  // namespace picgb

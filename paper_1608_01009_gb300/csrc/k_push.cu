@@ -1,0 +1,338 @@
+// Fused particle kernel: field gather, Boris push, move and Villasenor-Buneman
+// current deposition for one species, one supercell chunk per CTA iteration.
+//
+// Method (arXiv:1608.01009): Sec. 2 lists the stages -- interpolate the field
+// to each particle, solve the relativistic equations of motion, compute the
+// current density; Sec. 3 fixes the cloud-in-cell form factor, the
+// Villasenor-Buneman charge-conserving deposition and double precision; Sec. 4.3
+// groups particles by supercells so that a supercell's field and current data
+// stay in fast memory (there: L1; here: shared memory).
+//
+// GB300 design:
+//   * persistent CTAs (a multiple of the SM count) stride over a table of
+//     chunks (<= CHUNK particles of one supercell), built by the sort;
+//   * each chunk's (S+4)^3 x 6 field tile -- the supercell plus 2 cells each
+//     side -- arrives in shared memory in ONE 4-D TMA box load from the
+//     ghost-padded E|B buffer, completion on an mbarrier (bounded wait);
+//   * particles are read and written as coalesced SoA streams; positions are
+//     a packed global cell + an offset in the cell, so the FP64 path needs no
+//     double->int conversion (slower than an FMA on this part);
+//   * current goes to an (S+3)^3 x 3 shared-memory tile with shared atomics
+//     and is merged into the global FP64 J with one RED per non-zero node.
+//   R = double: every value in FP64.  R = float (mixed): offsets, momenta,
+//   field tile (from the FP32 field copy), interpolation and the shared J tile
+//   in FP32; the merge into J and the kinetic-energy sum in FP64.
+#include "pic_internal.cuh"
+
+namespace picgb {
+
+
+
+template <class R>
+__device__ __forceinline__ R lerp(R a, R b, R t) {
+    return fma(t, b - a, a);
+}
+
+// Trilinear interpolation from a T^3 tile at lattice base (i,j,k), fractions (a,b,c).
+template <class R, int T>
+__device__ __forceinline__ R tri(const R* __restrict__ F, int i, int j, int k, R a, R b, R c) {
+    const R* q = F + (k * T + j) * T + i;
+    R c00 = lerp(q[0], q[1], a);
+    R c10 = lerp(q[T], q[T + 1], a);
+    R c01 = lerp(q[T * T], q[T * T + 1], a);
+    R c11 = lerp(q[T * T + T], q[T * T + T + 1], a);
+    return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
+}
+
+// Current of a straight segment inside the cell whose J-tile corner is (jx,jy,jz):
+// start a (cell-relative), displacement d (cells).  Edge weights are the line
+// integrals of the two transverse CIC weights: W(s1) W(s2) + sigma dp dr / 12.
+template <class R, int TJ>
+__device__ __forceinline__ void segment(R* Jt, int jx, int jy, int jz, R ax, R ay, R az, R dx, R dy, R dz, R Qx,
+                                        R Qy, R Qz) {
+    constexpr int TJ2 = TJ * TJ, TJ3 = TJ * TJ * TJ;
+    const R h = R(0.5), tw = R(1.0 / 12.0);
+    R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
+    R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
+    int b = (jz * TJ + jy) * TJ + jx;
+    {  // Jx on edges (i+1/2, j+s1, k+s2)
+        R c = dy * dz * tw, q = Qx * dx;
+        R* J = Jt + b;
+        atomicAdd(J, q * fma(oy, oz, c));
+        atomicAdd(J + TJ, q * fma(my, oz, -c));
+        atomicAdd(J + TJ2, q * fma(oy, mz, -c));
+        atomicAdd(J + TJ + TJ2, q * fma(my, mz, c));
+    }
+    {  // Jy on edges (i+s1, j+1/2, k+s2)
+        R c = dx * dz * tw, q = Qy * dy;
+        R* J = Jt + TJ3 + b;
+        atomicAdd(J, q * fma(ox, oz, c));
+        atomicAdd(J + 1, q * fma(mx, oz, -c));
+        atomicAdd(J + TJ2, q * fma(ox, mz, -c));
+        atomicAdd(J + 1 + TJ2, q * fma(mx, mz, c));
+    }
+    {  // Jz on edges (i+s1, j+s2, k+1/2)
+        R c = dx * dy * tw, q = Qz * dz;
+        R* J = Jt + 2 * TJ3 + b;
+        atomicAdd(J, q * fma(ox, oy, c));
+        atomicAdd(J + 1, q * fma(mx, oy, -c));
+        atomicAdd(J + TJ, q * fma(ox, my, -c));
+        atomicAdd(J + 1 + TJ, q * fma(mx, my, c));
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void sort3(R& a, R& b, R& c) {
+    R lo = fmin(a, b), hi = fmax(a, b);
+    a = lo;
+    b = hi;
+    lo = fmin(b, c);
+    hi = fmax(b, c);
+    b = lo;
+    c = hi;
+    lo = fmin(a, b);
+    hi = fmax(a, b);
+    a = lo;
+    b = hi;
+}
+
+// Villasenor-Buneman split of a move that leaves its start cell: cut at every
+// face crossed (at most one per axis), pieces in order of the crossing
+// parameter, each piece deposited in the cell that contains its midpoint.
+template <class R, int TJ>
+__device__ __noinline__ void deposit_split(R* Jt, int jx, int jy, int jz, R ax, R ay, R az, R dx, R dy, R dz, R Qx,
+                                           R Qy, R Qz) {
+    R bx = ax + dx, by = ay + dy, bz = az + dz;
+    R t1 = (bx < R(0) || bx >= R(1)) ? ((bx >= R(1) ? R(1) : R(0)) - ax) / dx : R(1);
+    R t2 = (by < R(0) || by >= R(1)) ? ((by >= R(1) ? R(1) : R(0)) - ay) / dy : R(1);
+    R t3 = (bz < R(0) || bz >= R(1)) ? ((bz >= R(1) ? R(1) : R(0)) - az) / dz : R(1);
+    sort3(t1, t2, t3);
+    R ts[5] = {R(0), t1, t2, t3, R(1)};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        R ta = ts[s], tb = ts[s + 1];
+        if (!(tb > ta)) continue;
+        R pax = fma(ta, dx, ax), pay = fma(ta, dy, ay), paz = fma(ta, dz, az);
+        R pbx = fma(tb, dx, ax), pby = fma(tb, dy, ay), pbz = fma(tb, dz, az);
+        R mx = R(0.5) * (pax + pbx), my = R(0.5) * (pay + pby), mz = R(0.5) * (paz + pbz);
+        int ox = mx < R(0) ? -1 : (mx >= R(1) ? 1 : 0);
+        int oy = my < R(0) ? -1 : (my >= R(1) ? 1 : 0);
+        int oz = mz < R(0) ? -1 : (mz >= R(1) ? 1 : 0);
+        segment<R, TJ>(Jt, jx + ox, jy + oy, jz + oz, pax - R(ox), pay - R(oy), paz - R(oz), pbx - pax, pby - pay,
+                       pbz - paz, Qx, Qy, Qz);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ R below_one();
+template <>
+__device__ __forceinline__ double below_one<double>() {
+    return 0x1.fffffffffffffp-1;
+}
+template <>
+__device__ __forceinline__ float below_one<float>() {
+    return 0x1.fffffep-1f;
+}
+
+// New cell index along one axis after a displacement whose end point in the
+// start-cell frame is b: shift in {-1,0,1}, new offset in [0,1).
+template <class R>
+__device__ __forceinline__ int shift_of(R b, R& off) {
+    int s = b >= R(1) ? 1 : (b < R(0) ? -1 : 0);
+    R o = b - R(s);
+    off = o < below_one<R>() ? o : below_one<R>();
+    return s;
+}
+
+template <class R, int S>
+__device__ __forceinline__ double push_one(const R* __restrict__ F, R* Jt, const PStore<R>& ps, int p,
+                                           const PushParams& pp, int c0x, int c0y, int c0z, int* err) {
+    constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
+    const GridDev& g = pp.g;
+    int cp = ps.cell[p];
+    if (cp < 0) return 0.0;  // deactivated (left through an absorbing boundary)
+    int gx = cell_x(cp), gy = cell_y(cp), gz = cell_z(cp);
+    // cell relative to the supercell origin: the periodic image next to the tile
+    int lx = gx - c0x, ly = gy - c0y, lz = gz - c0z;
+    if (lx < -1) lx += g.n[0]; else if (lx > S) lx -= g.n[0];
+    if (ly < -1) ly += g.n[1]; else if (ly > S) ly -= g.n[1];
+    if (lz < -1) lz += g.n[2]; else if (lz > S) lz -= g.n[2];
+    if ((unsigned)(lx + 1) > (unsigned)(S + 1) || (unsigned)(ly + 1) > (unsigned)(S + 1) ||
+        (unsigned)(lz + 1) > (unsigned)(S + 1)) {
+        atomicOr(err, ERRBIT_DRIFT);
+        return 0.0;
+    }
+    R fx = ps.off[0][p], fy = ps.off[1][p], fz = ps.off[2][p];
+    R ux = ps.u[0][p], uy = ps.u[1][p], uz = ps.u[2][p];
+    const R w = ps.w[p];
+
+    // ---- gather: each component from its own staggered lattice (tile origin = cell c0-2)
+    const int tx = lx + 2, ty = ly + 2, tz = lz + 2;
+    const R hf = R(0.5);
+    const bool sxb = fx < hf, syb = fy < hf, szb = fz < hf;
+    const int hx = sxb ? tx - 1 : tx, hy = syb ? ty - 1 : ty, hz = szb ? tz - 1 : tz;
+    const R gxf = fx + (sxb ? hf : -hf), gyf = fy + (syb ? hf : -hf), gzf = fz + (szb ? hf : -hf);
+    const R Ex = tri<R, T>(F + 0 * T3, hx, ty, tz, gxf, fy, fz);
+    const R Ey = tri<R, T>(F + 1 * T3, tx, hy, tz, fx, gyf, fz);
+    const R Ez = tri<R, T>(F + 2 * T3, tx, ty, hz, fx, fy, gzf);
+    const R Bx = tri<R, T>(F + 3 * T3, tx, hy, hz, fx, gyf, gzf);
+    const R By = tri<R, T>(F + 4 * T3, hx, ty, hz, gxf, fy, gzf);
+    const R Bz = tri<R, T>(F + 5 * T3, hx, hy, tz, gxf, gyf, fz);
+
+    // ---- Boris: half electric kick, rotation, half electric kick
+    const R h = R(pp.qdt2m);
+    R umx = fma(h, Ex, ux), umy = fma(h, Ey, uy), umz = fma(h, Ez, uz);
+    R hg = h * rsqrt(fma(umx, umx, fma(umy, umy, fma(umz, umz, R(1)))));
+    R tbx = hg * Bx, tby = hg * By, tbz = hg * Bz;
+    R sf = R(2) / (R(1) + fma(tbx, tbx, fma(tby, tby, tbz * tbz)));
+    R sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
+    R upx = fma(umy, tbz, fma(-umz, tby, umx));
+    R upy = fma(umz, tbx, fma(-umx, tbz, umy));
+    R upz = fma(umx, tby, fma(-umy, tbx, umz));
+    ux = fma(h, Ex, fma(upy, sbz, fma(-upz, sby, umx)));
+    uy = fma(h, Ey, fma(upz, sbx, fma(-upx, sbz, umy)));
+    uz = fma(h, Ez, fma(upx, sby, fma(-upy, sbx, umz)));
+
+    // ---- move: displacement in cells, x^{n+1} = x^n + dt u / gamma
+    const R u2p1 = fma(ux, ux, fma(uy, uy, fma(uz, uz, R(1))));
+    const R gi = rsqrt(u2p1);
+    const R dx = ux * (gi * R(pp.dtd[0])), dy = uy * (gi * R(pp.dtd[1])), dz = uz * (gi * R(pp.dtd[2]));
+    const R bxr = fx + dx, byr = fy + dy, bzr = fz + dz;
+
+    // ---- new cell and offset; the end cell must stay inside the tiles' slack
+    R nfx, nfy, nfz;
+    const int sx = shift_of(bxr, nfx), sy = shift_of(byr, nfy), sz = shift_of(bzr, nfz);
+    if ((unsigned)(lx + sx + 1) > (unsigned)(S + 1) || (unsigned)(ly + sy + 1) > (unsigned)(S + 1) ||
+        (unsigned)(lz + sz + 1) > (unsigned)(S + 1)) {
+        // cannot happen while K * max(dt/d) < 1; record it, drop the particle, touch no tile
+        atomicOr(err, ERRBIT_DRIFT);
+        ps.cell[p] = INACTIVE | cp;
+        return 0.0;
+    }
+
+    // ---- Villasenor-Buneman deposit into the shared J tile (tile origin = cell c0-1)
+    if (w != R(0)) {
+        const R Qx = R(pp.cq[0]) * w, Qy = R(pp.cq[1]) * w, Qz = R(pp.cq[2]) * w;
+        const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
+        if ((sx | sy | sz) == 0)
+            segment<R, TJ>(Jt, jx, jy, jz, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+        else
+            deposit_split<R, TJ>(Jt, jx, jy, jz, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+    }
+
+    int ng[3] = {gx + sx, gy + sy, gz + sz};
+    bool gone = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (ng[a] < 0 || ng[a] >= g.n[a]) {
+            if (g.bc[a] == 0) ng[a] += ng[a] < 0 ? g.n[a] : -g.n[a];
+            else gone = true;
+        }
+    }
+    ps.cell[p] = gone ? (INACTIVE | cp) : pack_cell(ng[0], ng[1], ng[2]);
+    ps.off[0][p] = nfx;
+    ps.off[1][p] = nfy;
+    ps.off[2][p] = nfz;
+    ps.u[0][p] = ux;
+    ps.u[1][p] = uy;
+    ps.u[2][p] = uz;
+    // kinetic energy of the new state: w (gamma - 1), gamma = (1 + u^2) / sqrt(1 + u^2)
+    return gone ? 0.0 : (double)w * (double)fma(u2p1, gi, R(-1));
+}
+
+template <class R, int S, int NT>
+__global__ void __launch_bounds__(NT) k_push(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<R> ps,
+                                            const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
+                                            double* __restrict__ J, double* __restrict__ ek_part,
+                                            int* __restrict__ err) {
+    constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
+    extern __shared__ unsigned char smem_raw[];
+    R* F = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    R* Jt = F + 6 * T3;
+    __shared__ uint64_t bar;
+    __shared__ double red[NT / 32];
+    const GridDev& g = pp.g;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    double ek = 0.0;
+    const int nch = *nchunks;
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const Chunk ch = chunks[c];
+        const int sx = ch.sc % g.nsc[0], sy = (ch.sc / g.nsc[0]) % g.nsc[1], sz = ch.sc / (g.nsc[0] * g.nsc[1]);
+        const int c0x = sx * S, c0y = sy * S, c0z = sz * S;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar, 6u * T3 * (uint32_t)sizeof(R));
+            // field tile: cells c0-2 .. c0+S+1, i.e. padded index c0 .. c0+S+3
+            tma_load_4d(F, &tmEB, c0x, c0y, c0z, 0, &bar);
+        }
+        for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);
+        const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+            return;
+        }
+        phase ^= 1u;
+        const int end = ch.start + ch.count;
+        for (int p = ch.start + threadIdx.x; p < end; p += NT)
+            ek += push_one<R, S>(F, Jt, ps, p, pp, c0x, c0y, c0z, err);
+        __syncthreads();
+        // merge: J tile cell t is domain cell c0 - 1 + t, padded index c0 + 1 + t
+        for (int i = threadIdx.x; i < 3 * TJ3; i += NT) {
+            const R v = Jt[i];
+            if (v != R(0)) {
+                const int comp = i / TJ3, r = i - comp * TJ3;
+                const int tz = r / (TJ * TJ), ty = (r / TJ) % TJ, tx = r % TJ;
+                const long long o = (long long)comp * g.P + (c0x + 1 + tx) +
+                                    (long long)g.np[0] * ((c0y + 1 + ty) + (long long)g.np[1] * (c0z + 1 + tz));
+                atomicAdd(&J[o], (double)v);
+            }
+        }
+        __syncthreads();
+    }
+    const double s = block_sum<NT>(ek, red);
+    if (threadIdx.x == 0) ek_part[blockIdx.x] = s * pp.mass;
+}
+
+// ------------------------------------------------------------------ launchers
+constexpr int PUSH_NT = 256;
+
+template <class R, int S>
+size_t push_smem_bytes() {
+    constexpr int T = S + 4, TJ = S + 3;
+    return 128 + sizeof(R) * (6 * T * T * T + 3 * TJ * TJ * TJ);
+}
+
+template <class R, int S>
+cudaError_t push_setup(int* blocks_per_sm) {
+    auto k = k_push<R, S, PUSH_NT>;
+    size_t sm = push_smem_bytes<R, S>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, PUSH_NT, sm);
+}
+
+template <class R, int S>
+cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
+                        const Chunk* chunks, const int* nchunks, double* J, double* ek_part, int* err) {
+    k_push<R, S, PUSH_NT><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, chunks, nchunks, J, ek_part,
+                                                                         err);
+    return cudaGetLastError();
+}
+
+#define PICGB_PUSH_INST(R, S)                                                                                   \
+    template cudaError_t push_setup<R, S>(int*);                                                                \
+    template cudaError_t push_launch<R, S>(int, cudaStream_t, const CUtensorMap&, const PushParams&,            \
+                                           const PStore<R>&, const Chunk*, const int*, double*, double*, int*); \
+    template size_t push_smem_bytes<R, S>();
+PICGB_PUSH_INST(double, 2)
+PICGB_PUSH_INST(double, 4)
+PICGB_PUSH_INST(double, 8)
+PICGB_PUSH_INST(float, 4)
+PICGB_PUSH_INST(float, 8)
+
+}  // namespace picgb

@@ -1,0 +1,819 @@
+// C ABI of libpicgb (declared in include/pic.h): context, species stores,
+// step scheduling, diagnostics and error reporting.  Every compute step runs
+// in the CUDA kernels of this library; there is no host fallback.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.cuh"
+
+namespace picgb {
+
+// launchers defined in the kernel translation units
+cudaError_t fdtd_b_launch(cudaStream_t, double*, const GridDev&, double, int, float*, double*);
+cudaError_t fdtd_e_launch(cudaStream_t, double*, double*, double*, const GridDev&);
+cudaError_t refresh_launch(cudaStream_t, double*, const GridDev&, float*);
+cudaError_t field_energy_launch(cudaStream_t, const double*, const GridDev&, double*);
+int fdtd_blocks(const GridDev&);
+template <class R>
+cudaError_t sort_launch(cudaStream_t, int, const GridDev&, PStore<R>, PStore<R>, const long long*, long long*, int*,
+                        int*, int*, int*, Chunk*, int*);
+template <class R>
+cudaError_t load_launch(cudaStream_t, long long, const double* const*, const PStore<R>&, const GridDev&);
+template <class R>
+cudaError_t unload_launch(cudaStream_t, int, const PStore<R>&, const long long*, const GridDev&, int*, long long,
+                          long long*, double* const*);
+template <class R>
+cudaError_t count_launch(cudaStream_t, int, const PStore<R>&, const long long*, int*);
+template <class R>
+cudaError_t kinetic_launch(cudaStream_t, int, const PStore<R>&, const long long*, double, double*);
+cudaError_t energy_finalize_launch(cudaStream_t, const double*, int, const double*, int, double, double*);
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+template <class R>
+struct Store {
+    PStore<R> buf[2];
+    int cur = 0;
+    PStore<R>& a() { return buf[cur]; }
+    PStore<R>& b() { return buf[cur ^ 1]; }
+};
+
+struct Species {
+    double q = 0, m = 1;
+    long long cap = 0;
+    Store<double> s64;
+    Store<float> s32;
+    long long* d_n = nullptr;      // d_n[0] current count, d_n[1] count after the pending sort
+    int* d_bin_start = nullptr;
+    Chunk* d_chunks = nullptr;
+    int* d_nchunks = nullptr;
+    double* d_ek = nullptr;        // kinetic-energy partials of the last push (push_grid entries)
+    std::vector<void*> allocs;
+};
+
+}  // namespace picgb
+
+using namespace picgb;
+
+struct pic_ctx {
+    pic_grid_desc desc{};
+    GridDev g{};
+    cudaStream_t st = nullptr;
+    int dev = 0, nsm = 0;
+    bool mixed = false;
+    int K = 1, since_sort = 0;
+    long long steps = 0;
+    double* EB = nullptr;
+    double* J = nullptr;
+    double* Jlast = nullptr;
+    float* EB32 = nullptr;
+    CUtensorMap tm64{}, tm32{};
+    int push_grid = 0;
+    std::vector<Species> sp;
+    int* d_err = nullptr;
+    int* d_keys = nullptr;
+    long long keys_cap = 0;
+    int* d_counts = nullptr;
+    int* d_cursor = nullptr;
+    int* d_counter = nullptr;
+    double* d_wf = nullptr;     // field-energy partials (fdtd blocks)
+    double* d_ekall = nullptr;  // kinetic partials, contiguous over species
+    double* d_energy = nullptr; // [wf, wk] of the last finalize
+    bool energy_fresh = false;  // d_energy describes the current state
+    std::string err;
+    long long launches = 0;
+    bool timing = false;
+    double stage_ms[4] = {0, 0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(pic_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CUDA_TRY(c, call)                                                                             \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return fail((c), PIC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int dalloc(pic_ctx* c, std::vector<void*>& list, T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PIC_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    list.push_back(q);
+    *p = static_cast<T*>(q);
+    return PIC_OK;
+}
+
+int validate(const pic_grid_desc* g, pic_ctx* c) {
+    if (!g) return fail(c, PIC_ERR_ARG, "null descriptor");
+    int S = g->supercell;
+    if (g->precision != PIC_FP64 && g->precision != PIC_MIXED) return fail(c, PIC_ERR_ARG, "bad precision");
+    if (!(S == 4 || S == 8 || (S == 2 && g->precision == PIC_FP64)))
+        return fail(c, PIC_ERR_ARG, "supercell must be 4 or 8 (2 for FP64 only), got %d", S);
+    for (int a = 0; a < 3; ++a) {
+        if (g->n[a] < 4 || g->n[a] > 1024) return fail(c, PIC_ERR_ARG, "n[%d]=%d outside 4..1024", a, g->n[a]);
+        if (g->n[a] % S) return fail(c, PIC_ERR_ARG, "n[%d]=%d not a multiple of supercell %d", a, g->n[a], S);
+        if (!(g->d[a] > 0) || !std::isfinite(g->d[a])) return fail(c, PIC_ERR_ARG, "cell size d[%d] must be > 0", a);
+        if (g->bc[a] != PIC_BC_PERIODIC && g->bc[a] != PIC_BC_ABSORBING) return fail(c, PIC_ERR_ARG, "bad bc[%d]", a);
+        if (g->bc[a] == PIC_BC_ABSORBING && 2 * g->absorb_cells > g->n[a])
+            return fail(c, PIC_ERR_ARG, "absorbing layer wider than half the axis %d", a);
+    }
+    if (!(g->dt > 0) || !std::isfinite(g->dt)) return fail(c, PIC_ERR_ARG, "dt must be > 0");
+    if (g->absorb_cells < 0 || !(g->absorb_sigma >= 0 && g->absorb_sigma <= 1))
+        return fail(c, PIC_ERR_ARG, "absorbing layer: cells >= 0 and 0 <= sigma <= 1 required");
+    if ((long long)g->n[0] * g->n[1] * g->n[2] > (1LL << 30)) return fail(c, PIC_ERR_ARG, "grid too large");
+    double s = 0, dmax = 0;
+    for (int a = 0; a < 3; ++a) {
+        s += 1.0 / (g->d[a] * g->d[a]);
+        dmax = std::fmax(dmax, g->dt / g->d[a]);
+    }
+    double courant = g->dt * std::sqrt(s);
+    if (!(courant < 1.0)) return fail(c, PIC_ERR_CFL, "Courant number %.6f >= 1", courant);
+    if (g->sort_interval < 0) return fail(c, PIC_ERR_ARG, "sort_interval < 0");
+    if (g->sort_interval > 0 && !(g->sort_interval * dmax < 1.0))
+        return fail(c, PIC_ERR_CFL, "sort_interval %d * max(dt/d) = %.4f must be < 1 (supercell slack is one cell)",
+                    g->sort_interval, g->sort_interval * dmax);
+    if (g->precision == PIC_MIXED && S % 4) return fail(c, PIC_ERR_ARG, "mixed precision needs supercell 4 or 8");
+    return PIC_OK;
+}
+
+int encode_tmap(pic_ctx* c, CUtensorMap* map, void* base, bool fp32) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        CUDA_TRY(c, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !f) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    const GridDev& g = c->g;
+    const size_t es = fp32 ? 4 : 8;
+    const cuuint32_t T = (cuuint32_t)(g.S + 4);
+    cuuint64_t dims[4] = {(cuuint64_t)g.np[0], (cuuint64_t)g.np[1], (cuuint64_t)g.np[2], 6};
+    cuuint64_t strides[3] = {(cuuint64_t)g.np[0] * es, (cuuint64_t)g.np[0] * g.np[1] * es, (cuuint64_t)g.P * es};
+    cuuint32_t box[4] = {T, T, T, 6};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PIC_OK;
+}
+
+template <class R>
+int push_dispatch_setup(pic_ctx* c, int S, int* bps) {
+    cudaError_t e = cudaErrorInvalidValue;
+    if (S == 2) e = push_setup<double, 2>(bps);
+    if (S == 4) e = push_setup<R, 4>(bps);
+    if (S == 8) e = push_setup<R, 8>(bps);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push kernel setup: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+PushParams make_params(const pic_ctx* c, const Species& s) {
+    PushParams pp;
+    pp.g = c->g;
+    pp.qdt2m = 0.5 * s.q * c->g.dt / s.m;
+    for (int a = 0; a < 3; ++a) {
+        pp.dtd[a] = c->g.dt / c->g.d[a];
+        pp.cq[a] = s.q / (c->g.dt * c->g.d[(a + 1) % 3] * c->g.d[(a + 2) % 3]);
+    }
+    pp.mass = s.m;
+    return pp;
+}
+
+void stage_begin(pic_ctx* c, int stage, cudaEvent_t* e0) {
+    if (!c->timing) return;
+    cudaEventCreate(e0);
+    cudaEventRecord(*e0, c->st);
+    (void)stage;
+}
+
+void stage_end(pic_ctx* c, int stage, cudaEvent_t e0) {
+    if (!c->timing) return;
+    cudaEvent_t e1;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, c->st);
+    c->ev[stage].push_back({e0, e1});
+}
+
+template <class R>
+Store<R>& store_of(Species& s);
+template <>
+Store<double>& store_of<double>(Species& s) { return s.s64; }
+template <>
+Store<float>& store_of<float>(Species& s) { return s.s32; }
+
+template <class R>
+int sort_species(pic_ctx* c, Species& s) {
+    Store<R>& st = store_of<R>(s);
+    cudaError_t e = sort_launch<R>(c->st, c->nsm, c->g, st.a(), st.b(), s.d_n, s.d_n + 1, c->d_keys, c->d_counts,
+                                   c->d_cursor, s.d_bin_start, s.d_chunks, s.d_nchunks);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "sort launch: %s", cudaGetErrorString(e));
+    c->launches += 3;
+    st.cur ^= 1;
+    CUDA_TRY(c, cudaMemcpyAsync(s.d_n, s.d_n + 1, sizeof(long long), cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
+int sort_all(pic_ctx* c) {
+    for (auto& s : c->sp) {
+        int r = c->mixed ? sort_species<float>(c, s) : sort_species<double>(c, s);
+        if (r) return r;
+    }
+    c->since_sort = 0;
+    return PIC_OK;
+}
+
+template <class R>
+int push_species(pic_ctx* c, Species& s) {
+    PushParams pp = make_params(c, s);
+    const CUtensorMap& tm = c->mixed ? c->tm32 : c->tm64;
+    cudaError_t e = cudaErrorInvalidValue;
+    PStore<R>& ps = store_of<R>(s).a();
+    const int S = c->g.S;
+    if constexpr (sizeof(R) == 8) {
+        if (S == 2) e = push_launch<double, 2>(c->push_grid, c->st, tm, pp, ps, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+    }
+    if (S == 4) e = push_launch<R, 4>(c->push_grid, c->st, tm, pp, ps, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+    if (S == 8) e = push_launch<R, 8>(c->push_grid, c->st, tm, pp, ps, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push launch: %s", cudaGetErrorString(e));
+    c->launches += 1;
+    return PIC_OK;
+}
+
+template <class R>
+int alloc_store(pic_ctx* c, Species& s, Store<R>& st, long long cap) {
+    for (int b = 0; b < 2; ++b) {
+        PStore<R>& p = st.buf[b];
+        int r = dalloc(c, s.allocs, &p.cell, cap);
+        for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, s.allocs, &p.off[a], cap);
+        for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, s.allocs, &p.u[a], cap);
+        if (!r) r = dalloc(c, s.allocs, &p.w, cap);
+        if (!r) r = dalloc(c, s.allocs, &p.id, cap);
+        if (r) return r;
+    }
+    st.cur = 0;
+    return PIC_OK;
+}
+
+void free_species(Species& s) {
+    for (void* p : s.allocs) cudaFree(p);
+    s.allocs.clear();
+}
+
+int ensure_keys(pic_ctx* c, long long n) {
+    if (n <= c->keys_cap) return PIC_OK;
+    if (c->d_keys) {
+        cudaStreamSynchronize(c->st);
+        cudaFree(c->d_keys);
+        for (auto& p : c->allocs)
+            if (p == c->d_keys) p = nullptr;
+        c->d_keys = nullptr;
+    }
+    int r = dalloc(c, c->allocs, &c->d_keys, (size_t)n);
+    if (r) return r;
+    c->keys_cap = n;
+    return PIC_OK;
+}
+
+// (Re)load the particles of species s from FP64 arrays (host or device).
+int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src, bool device) {
+    if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", n);
+    for (int k = 0; k < 7 && n > 0; ++k)
+        if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array %d", k);
+    if (!s.d_n || n > s.cap) {
+        cudaStreamSynchronize(c->st);
+        free_species(s);
+        long long cap = n > 0 ? n : 1;
+        s.cap = cap;
+        int r = dalloc(c, s.allocs, &s.d_n, 2);
+        if (!r) r = dalloc(c, s.allocs, &s.d_bin_start, (size_t)c->g.nbins + 1);
+        if (!r) r = dalloc(c, s.allocs, &s.d_chunks, (size_t)(c->g.nbins + cap / CHUNK + 1));
+        if (!r) r = dalloc(c, s.allocs, &s.d_nchunks, 1);
+        if (!r) r = c->mixed ? alloc_store(c, s, s.s32, cap) : alloc_store(c, s, s.s64, cap);
+        if (r) return r;
+    }
+    long long kmax = 0;
+    for (auto& o : c->sp) kmax = o.cap > kmax ? o.cap : kmax;
+    int r = ensure_keys(c, kmax > s.cap ? kmax : s.cap);
+    if (r) return r;
+    // stage FP64 inputs on the device when they come from the host
+    std::vector<double*> tmp;
+    const double* dsrc[7];
+    if (!device && n > 0) {
+        for (int k = 0; k < 7; ++k) {
+            double* d = nullptr;
+            if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                for (double* t : tmp) cudaFree(t);
+                return fail(c, PIC_ERR_OOM, "staging buffer");
+            }
+            tmp.push_back(d);
+            cudaMemcpyAsync(d, src[k], n * sizeof(double), cudaMemcpyHostToDevice, c->st);
+            dsrc[k] = d;
+        }
+    } else {
+        for (int k = 0; k < 7; ++k) dsrc[k] = src[k];
+    }
+    long long nn = n;
+    CUDA_TRY(c, cudaMemcpyAsync(s.d_n, &nn, sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    cudaError_t e = c->mixed ? load_launch<float>(c->st, n, dsrc, s.s32.a(), c->g)
+                             : load_launch<double>(c->st, n, dsrc, s.s64.a(), c->g);
+    c->launches += n > 0 ? 1 : 0;
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "load: %s", cudaGetErrorString(e));
+    // bin the new particles; the other species are re-sorted too, so that every
+    // species starts the next sort interval together
+    r = sort_all(c);
+    if (!tmp.empty()) {
+        cudaStreamSynchronize(c->st);
+        for (double* t : tmp) cudaFree(t);
+    }
+    c->energy_fresh = false;
+    return r;
+}
+
+int add_species_impl(pic_ctx* c, const pic_species_desc* d, int64_t n, const double* const* src, bool device,
+                     int* id) {
+    if (!c) return PIC_ERR_ARG;
+    if (!d || !id) return fail(c, PIC_ERR_ARG, "null argument");
+    if (!(d->m > 0) || !std::isfinite(d->q)) return fail(c, PIC_ERR_ARG, "species mass must be > 0");
+    if ((int)c->sp.size() >= MAX_SPECIES) return fail(c, PIC_ERR_ARG, "too many species");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    c->sp.emplace_back();
+    Species& s = c->sp.back();
+    s.q = d->q;
+    s.m = d->m;
+    // kinetic partial slots for this species
+    int r = load_particles(c, s, n, src, device);
+    if (r) {
+        free_species(s);
+        c->sp.pop_back();
+        return r;
+    }
+    // rebuild the contiguous kinetic-partials buffer
+    if (c->d_ekall) {
+        cudaStreamSynchronize(c->st);
+        cudaFree(c->d_ekall);
+        for (auto& p : c->allocs)
+            if (p == c->d_ekall) p = nullptr;
+    }
+    r = dalloc(c, c->allocs, &c->d_ekall, (size_t)c->push_grid * c->sp.size());
+    if (r) return r;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_ekall, 0, sizeof(double) * c->push_grid * c->sp.size(), c->st));
+    for (size_t i = 0; i < c->sp.size(); ++i) c->sp[i].d_ek = c->d_ekall + i * c->push_grid;
+    *id = (int)c->sp.size() - 1;
+    if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+// 3-D copies between the unpadded ABI layout and a padded component.
+cudaMemcpy3DParms copy_params(const GridDev& g, void* padded, void* flat, bool to_padded) {
+    cudaMemcpy3DParms p;
+    memset(&p, 0, sizeof p);
+    cudaPitchedPtr pp = make_cudaPitchedPtr(padded, g.np[0] * sizeof(double), g.np[0], g.np[1]);
+    cudaPitchedPtr fp = make_cudaPitchedPtr(flat, g.n[0] * sizeof(double), g.n[0], g.n[1]);
+    if (to_padded) {
+        p.srcPtr = fp;
+        p.dstPtr = pp;
+        p.dstPos = make_cudaPos(PAD * sizeof(double), PAD, PAD);
+    } else {
+        p.srcPtr = pp;
+        p.srcPos = make_cudaPos(PAD * sizeof(double), PAD, PAD);
+        p.dstPtr = fp;
+    }
+    p.extent = make_cudaExtent(g.n[0] * sizeof(double), g.n[1], g.n[2]);
+    p.kind = cudaMemcpyDefault;
+    return p;
+}
+
+int set_fields_impl(pic_ctx* c, const double* const E[3], const double* const B[3], bool device) {
+    if (!c) return PIC_ERR_ARG;
+    if (!E || !B) return fail(c, PIC_ERR_ARG, "null field array");
+    for (int k = 0; k < 3; ++k)
+        if (!E[k] || !B[k]) return fail(c, PIC_ERR_ARG, "null field component");
+    for (int k = 0; k < 6; ++k) {
+        const double* src = k < 3 ? E[k] : B[k - 3];
+        cudaMemcpy3DParms p = copy_params(c->g, c->EB + k * c->g.P, const_cast<double*>(src), true);
+        CUDA_TRY(c, cudaMemcpy3DAsync(&p, c->st));
+    }
+    CUDA_TRY(c, refresh_launch(c->st, c->EB, c->g, c->EB32));
+    c->launches += 1;
+    c->energy_fresh = false;
+    if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int get_fields_impl(pic_ctx* c, double* const E[3], double* const B[3], bool device) {
+    if (!c) return PIC_ERR_ARG;
+    if (!E || !B) return fail(c, PIC_ERR_ARG, "null field array");
+    for (int k = 0; k < 6; ++k) {
+        double* dst = k < 3 ? E[k] : B[k - 3];
+        if (!dst) return fail(c, PIC_ERR_ARG, "null field component");
+        cudaMemcpy3DParms p = copy_params(c->g, c->EB + k * c->g.P, dst, false);
+        CUDA_TRY(c, cudaMemcpy3DAsync(&p, c->st));
+    }
+    if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int get_current_impl(pic_ctx* c, double* const J[3], bool device) {
+    if (!c) return PIC_ERR_ARG;
+    if (!J) return fail(c, PIC_ERR_ARG, "null current array");
+    const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    for (int k = 0; k < 3; ++k) {
+        if (!J[k]) return fail(c, PIC_ERR_ARG, "null current component");
+        CUDA_TRY(c, cudaMemcpyAsync(J[k], c->Jlast + k * ncell, ncell * sizeof(double), cudaMemcpyDefault, c->st));
+    }
+    if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int device_status(pic_ctx* c) {
+    int flags = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (flags & ERRBIT_TIMEOUT) return fail(c, PIC_ERR_TIMEOUT, "a bounded TMA/mbarrier wait expired in a kernel");
+    if (flags & ERRBIT_DRIFT)
+        return fail(c, PIC_ERR_BIN_OVERFLOW, "a particle left its supercell slack between sorts");
+    if (flags & ERRBIT_NAN) return fail(c, PIC_ERR_NAN, "non-finite value");
+    return PIC_OK;
+}
+
+template <class R>
+int get_particles_impl(pic_ctx* c, int species, int64_t cap, int64_t* n, int64_t* id, double* const* dst,
+                       bool device) {
+    Species& s = c->sp[species];
+    PStore<R>& ps = store_of<R>(s).a();
+    CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->st));
+    long long* did = reinterpret_cast<long long*>(id);
+    double* ddst[7];
+    std::vector<void*> tmp;
+    if (!device) {
+        // stage on the device, then copy back
+        long long m = cap > 0 ? cap : 1;
+        void* q = nullptr;
+        if (cudaMalloc(&q, m * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PIC_ERR_OOM, "staging");
+        }
+        tmp.push_back(q);
+        did = (long long*)q;
+        for (int k = 0; k < 7; ++k) {
+            if (cudaMalloc(&q, m * sizeof(double)) != cudaSuccess) {
+                cudaGetLastError();
+                for (void* t : tmp) cudaFree(t);
+                return fail(c, PIC_ERR_OOM, "staging");
+            }
+            tmp.push_back(q);
+            ddst[k] = (double*)q;
+        }
+    } else {
+        for (int k = 0; k < 7; ++k) ddst[k] = dst[k];
+    }
+    cudaError_t e = unload_launch<R>(c->st, c->nsm, ps, s.d_n, c->g, c->d_counter, cap, did, ddst);
+    c->launches += 1;
+    int cnt = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, c->d_counter, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess && !device && cnt > 0) {
+        long long m = cnt < cap ? cnt : cap;
+        cudaMemcpyAsync(id, did, m * sizeof(long long), cudaMemcpyDeviceToHost, c->st);
+        for (int k = 0; k < 7; ++k)
+            cudaMemcpyAsync(dst[k], ddst[k], m * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+        e = cudaStreamSynchronize(c->st);
+    }
+    for (void* t : tmp) cudaFree(t);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "get_particles: %s", cudaGetErrorString(e));
+    *n = cnt;
+    if (cnt > cap) return fail(c, PIC_ERR_ARG, "cap %lld < %d active particles", (long long)cap, cnt);
+    return PIC_OK;
+}
+
+int finalize_energy(pic_ctx* c, int nwf) {
+    const int nek = c->push_grid * (int)c->sp.size();
+    cudaError_t e = energy_finalize_launch(c->st, c->d_wf, nwf, c->d_ekall, nek,
+                                           0.5 * c->g.d[0] * c->g.d[1] * c->g.d[2], c->d_energy);
+    c->launches += 1;
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "energy finalize: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    pic_ctx tmp;
+    int r = validate(gd, &tmp);
+    if (r) {
+        fprintf(stderr, "pic_create: %s\n", tmp.err.c_str());
+        return r;
+    }
+    pic_ctx* c = new pic_ctx();
+    c->desc = *gd;
+    c->dev = gd->device;
+    c->st = reinterpret_cast<cudaStream_t>(gd->stream);
+    c->mixed = gd->precision == PIC_MIXED;
+    GridDev& g = c->g;
+    double dmax = 0;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = gd->n[a];
+        g.np[a] = gd->n[a] + 2 * PAD;
+        g.d[a] = gd->d[a];
+        g.bc[a] = gd->bc[a];
+        g.nsc[a] = gd->n[a] / gd->supercell;
+        dmax = std::fmax(dmax, gd->dt / gd->d[a]);
+    }
+    g.P = (long long)g.np[0] * g.np[1] * g.np[2];
+    g.dt = gd->dt;
+    g.S = gd->supercell;
+    g.nbins = g.nsc[0] * g.nsc[1] * g.nsc[2];
+    g.absorb_cells = gd->absorb_cells;
+    g.absorb_sigma = gd->absorb_sigma;
+    c->K = gd->sort_interval > 0 ? gd->sort_interval : (int)std::floor((1.0 - 1e-9) / dmax);
+    if (c->K < 1) c->K = 1;
+    auto bail = [&](int code) {
+        pic_destroy(c);
+        return code;
+    };
+    cudaError_t e = cudaSetDevice(c->dev);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "pic_create: cudaSetDevice(%d): %s\n", c->dev, cudaGetErrorString(e));
+        delete c;
+        return PIC_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    if ((r = dalloc(c, c->allocs, &c->EB, 6 * g.P))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->J, 3 * g.P))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->Jlast, 3 * ncell))) return bail(r);
+    if (c->mixed && (r = dalloc(c, c->allocs, &c->EB32, 6 * g.P))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_err, 1))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_counts, g.nbins))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_cursor, g.nbins))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_counter, 1))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_wf, fdtd_blocks(g)))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_energy, 2))) return bail(r);
+    cudaMemsetAsync(c->EB, 0, 6 * g.P * sizeof(double), c->st);
+    cudaMemsetAsync(c->J, 0, 3 * g.P * sizeof(double), c->st);
+    cudaMemsetAsync(c->Jlast, 0, 3 * ncell * sizeof(double), c->st);
+    if (c->EB32) cudaMemsetAsync(c->EB32, 0, 6 * g.P * sizeof(float), c->st);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    cudaMemsetAsync(c->d_counts, 0, g.nbins * sizeof(int), c->st);
+    cudaMemsetAsync(c->d_energy, 0, 2 * sizeof(double), c->st);
+    if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) {
+        fail(c, PIC_ERR_CUDA, "init: %s", cudaGetErrorString(e));
+        return bail(PIC_ERR_CUDA);
+    }
+    if ((r = encode_tmap(c, &c->tm64, c->EB, false))) return bail(r);
+    if (c->mixed && (r = encode_tmap(c, &c->tm32, c->EB32, true))) return bail(r);
+    int bps = 0;
+    if ((r = c->mixed ? push_dispatch_setup<float>(c, g.S, &bps) : push_dispatch_setup<double>(c, g.S, &bps)))
+        return bail(r);
+    if (bps < 1) bps = 1;
+    c->push_grid = c->nsm * bps;
+    *out = c;
+    return PIC_OK;
+}
+
+int pic_destroy(pic_ctx* c) {
+    if (!c) return PIC_ERR_ARG;
+    cudaSetDevice(c->dev);
+    cudaStreamSynchronize(c->st);
+    for (auto& s : c->sp) free_species(s);
+    for (void* p : c->allocs)
+        if (p) cudaFree(p);
+    for (auto& v : c->ev)
+        for (auto& pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    delete c;
+    return PIC_OK;
+}
+
+const char* pic_last_error(const pic_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pic_add_species(pic_ctx* c, const pic_species_desc* s, int64_t n, const double* x, const double* y,
+                    const double* z, const double* ux, const double* uy, const double* uz, const double* w,
+                    int* species_id) {
+    const double* src[7] = {x, y, z, ux, uy, uz, w};
+    return add_species_impl(c, s, n, src, false, species_id);
+}
+
+int pic_add_species_dev(pic_ctx* c, const pic_species_desc* s, int64_t n, const double* x, const double* y,
+                        const double* z, const double* ux, const double* uy, const double* uz, const double* w,
+                        int* species_id) {
+    const double* src[7] = {x, y, z, ux, uy, uz, w};
+    return add_species_impl(c, s, n, src, true, species_id);
+}
+
+static int set_particles_impl(pic_ctx* c, int species, int64_t n, const double* const* src, bool device) {
+    if (!c) return PIC_ERR_ARG;
+    if (species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    int r = load_particles(c, c->sp[species], n, src, device);
+    if (r) return r;
+    if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int pic_set_particles(pic_ctx* c, int species, int64_t n, const double* x, const double* y, const double* z,
+                      const double* ux, const double* uy, const double* uz, const double* w) {
+    const double* src[7] = {x, y, z, ux, uy, uz, w};
+    return set_particles_impl(c, species, n, src, false);
+}
+
+int pic_set_particles_dev(pic_ctx* c, int species, int64_t n, const double* x, const double* y, const double* z,
+                          const double* ux, const double* uy, const double* uz, const double* w) {
+    const double* src[7] = {x, y, z, ux, uy, uz, w};
+    return set_particles_impl(c, species, n, src, true);
+}
+
+int pic_count_particles(pic_ctx* c, int species, int64_t* n) {
+    if (!c) return PIC_ERR_ARG;
+    if (!n || species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species or null n");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->st));
+    Species& s = c->sp[species];
+    cudaError_t e = c->mixed ? count_launch<float>(c->st, c->nsm, s.s32.a(), s.d_n, c->d_counter)
+                             : count_launch<double>(c->st, c->nsm, s.s64.a(), s.d_n, c->d_counter);
+    c->launches += 1;
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "count: %s", cudaGetErrorString(e));
+    int cnt = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&cnt, c->d_counter, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    *n = cnt;
+    return PIC_OK;
+}
+
+static int get_particles_any(pic_ctx* c, int species, int64_t cap, int64_t* n, int64_t* id, double* x, double* y,
+                             double* z, double* ux, double* uy, double* uz, double* w, bool device) {
+    if (!c) return PIC_ERR_ARG;
+    if (!n || !id || !x || !y || !z || !ux || !uy || !uz || !w) return fail(c, PIC_ERR_ARG, "null output array");
+    if (species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    double* dst[7] = {x, y, z, ux, uy, uz, w};
+    return c->mixed ? get_particles_impl<float>(c, species, cap, n, id, dst, device)
+                    : get_particles_impl<double>(c, species, cap, n, id, dst, device);
+}
+
+int pic_get_particles(pic_ctx* c, int species, int64_t cap, int64_t* n, int64_t* id, double* x, double* y,
+                      double* z, double* ux, double* uy, double* uz, double* w) {
+    return get_particles_any(c, species, cap, n, id, x, y, z, ux, uy, uz, w, false);
+}
+
+int pic_get_particles_dev(pic_ctx* c, int species, int64_t cap, int64_t* n, int64_t* id, double* x, double* y,
+                          double* z, double* ux, double* uy, double* uz, double* w) {
+    return get_particles_any(c, species, cap, n, id, x, y, z, ux, uy, uz, w, true);
+}
+
+int pic_set_fields(pic_ctx* c, const double* const E[3], const double* const B[3]) {
+    return set_fields_impl(c, E, B, false);
+}
+int pic_set_fields_dev(pic_ctx* c, const double* const E[3], const double* const B[3]) {
+    return set_fields_impl(c, E, B, true);
+}
+int pic_get_fields(pic_ctx* c, double* const E[3], double* const B[3]) { return get_fields_impl(c, E, B, false); }
+int pic_get_fields_dev(pic_ctx* c, double* const E[3], double* const B[3]) { return get_fields_impl(c, E, B, true); }
+int pic_get_current(pic_ctx* c, double* const J[3]) { return get_current_impl(c, J, false); }
+int pic_get_current_dev(pic_ctx* c, double* const J[3]) { return get_current_impl(c, J, true); }
+
+int pic_step(pic_ctx* c, int nsteps) {
+    if (!c) return PIC_ERR_ARG;
+    if (nsteps < 0) return fail(c, PIC_ERR_ARG, "nsteps < 0");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    const double h = 0.5 * c->g.dt;
+    const int nwf = fdtd_blocks(c->g);
+    for (int t = 0; t < nsteps; ++t) {
+        cudaEvent_t e0 = nullptr;
+        if (c->since_sort >= c->K) {
+            stage_begin(c, 2, &e0);
+            int r = sort_all(c);
+            if (r) return r;
+            stage_end(c, 2, e0);
+        }
+        stage_begin(c, 0, &e0);
+        for (auto& s : c->sp) {
+            int r = c->mixed ? push_species<float>(c, s) : push_species<double>(c, s);
+            if (r) return r;
+        }
+        stage_end(c, 0, e0);
+        stage_begin(c, 1, &e0);
+        CUDA_TRY(c, fdtd_b_launch(c->st, c->EB, c->g, h, 0, nullptr, nullptr));
+        CUDA_TRY(c, fdtd_e_launch(c->st, c->EB, c->J, c->Jlast, c->g));
+        CUDA_TRY(c, fdtd_b_launch(c->st, c->EB, c->g, h, 1, c->EB32, c->d_wf));
+        c->launches += 3;
+        stage_end(c, 1, e0);
+        stage_begin(c, 3, &e0);
+        int r = finalize_energy(c, nwf);
+        if (r) return r;
+        stage_end(c, 3, e0);
+        c->energy_fresh = true;
+        c->since_sort += 1;
+        c->steps += 1;
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_ctx* c) {
+    if (!c) return PIC_ERR_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    return device_status(c);
+}
+
+int pic_energy(pic_ctx* c, double* wf, double* wk) {
+    if (!c) return PIC_ERR_ARG;
+    if (!wf || !wk) return fail(c, PIC_ERR_ARG, "null output");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    if (!c->energy_fresh) {
+        CUDA_TRY(c, field_energy_launch(c->st, c->EB, c->g, c->d_wf));
+        c->launches += 1;
+        for (auto& s : c->sp) {
+            cudaError_t e = c->mixed ? kinetic_launch<float>(c->st, c->push_grid, s.s32.a(), s.d_n, s.m, s.d_ek)
+                                     : kinetic_launch<double>(c->st, c->push_grid, s.s64.a(), s.d_n, s.m, s.d_ek);
+            c->launches += 1;
+            if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "kinetic: %s", cudaGetErrorString(e));
+        }
+        int r = finalize_energy(c, fdtd_blocks(c->g));
+        if (r) return r;
+        c->energy_fresh = true;
+    }
+    double out[2];
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->d_energy, sizeof out, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    *wf = out[0];
+    *wk = out[1];
+    if (!std::isfinite(out[0]) || !std::isfinite(out[1])) {
+        int one = ERRBIT_NAN;
+        cudaMemcpy(c->d_err, &one, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(c, PIC_ERR_NAN, "non-finite energy (wf=%g, wk=%g)", out[0], out[1]);
+    }
+    return device_status(c);
+}
+
+int pic_enable_timing(pic_ctx* c, int on) {
+    if (!c) return PIC_ERR_ARG;
+    c->timing = on != 0;
+    return PIC_OK;
+}
+
+int pic_stage_times(pic_ctx* c, double out[4]) {
+    if (!c) return PIC_ERR_ARG;
+    if (!out) return fail(c, PIC_ERR_ARG, "null output");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    for (int s = 0; s < 4; ++s) {
+        for (auto& pr : c->ev[s]) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            c->stage_ms[s] += ms;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        c->ev[s].clear();
+        out[s] = c->stage_ms[s];
+    }
+    return PIC_OK;
+}
+
+int pic_launch_count(pic_ctx* c, int64_t* n, int reset) {
+    if (!c) return PIC_ERR_ARG;
+    if (!n) return fail(c, PIC_ERR_ARG, "null output");
+    *n = c->launches;
+    if (reset) c->launches = 0;
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Internal layouts and device helpers of libpicgb (not part of the C ABI).
+//
+// HBM layout
+//   fields  FP64, one ghost-padded array per component, PAD = 2 ghost cells on
+//           each side: padded extent np[a] = n[a] + 4, element (i,j,k) of the
+//           domain at (i+2) + np0*((j+2) + np1*(k+2)).  E and B live in one
+//           buffer EB of 6 consecutive components (Ex Ey Ez Bx By Bz), so one
+//           4-D TMA box (x, y, z, component) stages a supercell's whole field
+//           tile.  J (3 components) is a separate padded buffer that the
+//           particle kernels add into; its ghost cells are folded onto their
+//           periodic owners by the E update.  Mixed mode keeps an FP32 copy of
+//           EB with the same geometry.
+//   particles  structure of arrays, binned by supercell: per particle a
+//           packed global cell index (10 bits per axis, sign bit = inactive),
+//           the offset inside the cell (3 x R, in [0,1)), momentum u (3 x R),
+//           weight (R) and an id (int32), R = double (FP64) or float (mixed).
+//           bin_start[b] .. bin_start[b+1] are the particles of supercell b.
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace picgb {
+
+constexpr int PAD = 2;
+constexpr int MAX_SPECIES = 8;
+
+// Sticky device error bits (the host maps them to pic_status codes).
+enum : int { ERRBIT_DRIFT = 1, ERRBIT_TIMEOUT = 2, ERRBIT_NAN = 4 };
+
+constexpr int INACTIVE = (int)0x80000000;
+
+struct GridDev {
+    int n[3];      // cells
+    int np[3];     // padded extent n + 2 PAD
+    long long P;   // padded volume
+    double d[3];
+    double dt;
+    int bc[3];
+    int S;         // supercell edge in cells
+    int nsc[3];    // supercells per axis
+    int nbins;
+    int absorb_cells;
+    double absorb_sigma;
+};
+
+template <class R>
+struct PStore {
+    int* cell;     // packed global cell, INACTIVE bit
+    R* off[3];     // offset in cell, [0,1)
+    R* u[3];       // momentum u = gamma v / c
+    R* w;          // weight
+    int* id;
+};
+
+struct Chunk {
+    int sc;        // supercell (bin) index
+    int start;     // first particle
+    int count;     // particles in this chunk
+    int pad;
+};
+
+struct PushParams {
+    GridDev g;
+    double qdt2m;   // q dt / (2 m)
+    double dtd[3];  // dt / d[a]: velocity (in c) -> displacement in cells
+    double cq[3];   // q / (dt d[p] d[r]): current density per unit weight and cell displacement
+    double mass;
+};
+
+constexpr int CHUNK = 4096;  // most particles of one supercell handled by one CTA pass
+
+__host__ __device__ inline int pack_cell(int ix, int iy, int iz) { return ix | (iy << 10) | (iz << 20); }
+__host__ __device__ inline int cell_x(int c) { return c & 1023; }
+__host__ __device__ inline int cell_y(int c) { return (c >> 10) & 1023; }
+__host__ __device__ inline int cell_z(int c) { return (c >> 20) & 1023; }
+
+__host__ __device__ inline long long pidx(const GridDev& g, int i, int j, int k) {
+    // padded linear index of domain cell (i,j,k) (ghosts: i in [-PAD, n+PAD))
+    return (long long)(i + PAD) + (long long)g.np[0] * ((long long)(j + PAD) + (long long)g.np[1] * (k + PAD));
+}
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase: returns false if `limit` polls pass
+// without completion (the caller records a timeout and leaves).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint32_t limit) {
+    uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 4-D tiled TMA load global -> shared, completion signalled on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Poll budget of a TMA wait: far beyond any legitimate latency (each try_wait
+// may itself suspend for a while), short enough to return within seconds.
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+// ------------------------------------------------------------------ warp helpers
+// Warp-aggregated atomic add of 1 per lane on counters[key] (lanes with the
+// same key are served by one atomic); returns each lane's slot.  All 32 lanes
+// must call it; lanes with key < 0 take no slot and get -1.
+__device__ __forceinline__ int warp_agg_slot(int* counters, int key) {
+    unsigned peers = __match_any_sync(0xffffffffu, key);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader && key >= 0) base = atomicAdd(&counters[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return key >= 0 ? base + rank : -1;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Fixed-order block sum (deterministic for a fixed block size); result valid in thread 0.
+template <int NT>
+__device__ double block_sum(double v, double* scratch) {
+    v = warp_sum(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NT / 32; ++i) s += scratch[i];
+    return s;
+}
+
+// ------------------------------------------------------------------ launchers (host)
+template <class R, int S>
+cudaError_t push_setup(int* blocks_per_sm);
+template <class R, int S>
+cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
+                        const Chunk* chunks, const int* nchunks, double* J, double* ek_part, int* err);
+
+}  // namespace picgb

@@ -1,0 +1,278 @@
+"""Thin ctypes binding over libpicgb.so (C ABI in include/pic.h).
+
+Argument marshalling only: every step of the particle-in-cell path runs in the
+library's CUDA kernels.  Device buffers may be torch CUDA tensors (the "_dev"
+entry points receive their data pointers) and the context works on the torch
+stream it was created with.  If the library has not been built, or no CUDA
+device is present, the calls raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpicgb.so")
+
+PIC_OK = 0
+STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_BIN_OVERFLOW",
+          -5: "PIC_ERR_NAN", -6: "PIC_ERR_CUDA", -7: "PIC_ERR_STATE", -8: "PIC_ERR_TIMEOUT"}
+FP64, MIXED = 0, 1
+PERIODIC, ABSORBING = 0, 1
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("d", C.c_double * 3), ("dt", C.c_double), ("bc", C.c_int32 * 3),
+                ("absorb_cells", C.c_int32), ("absorb_sigma", C.c_double), ("precision", C.c_int32),
+                ("supercell", C.c_int32), ("sort_interval", C.c_int32), ("device", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class SpeciesDesc(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double)]
+
+
+_VP = C.c_void_p
+_P3 = _VP * 3
+_lib = None
+
+# name -> argtypes (all return int except pic_last_error)
+SIGNATURES = {
+    "pic_create": [C.POINTER(GridDesc), C.POINTER(_VP)],
+    "pic_destroy": [_VP],
+    "pic_last_error": [_VP],
+    "pic_add_species": [_VP, C.POINTER(SpeciesDesc), C.c_int64] + [_VP] * 7 + [C.POINTER(C.c_int)],
+    "pic_add_species_dev": [_VP, C.POINTER(SpeciesDesc), C.c_int64] + [_VP] * 7 + [C.POINTER(C.c_int)],
+    "pic_set_particles": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
+    "pic_set_particles_dev": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
+    "pic_count_particles": [_VP, C.c_int, C.POINTER(C.c_int64)],
+    "pic_get_particles": [_VP, C.c_int, C.c_int64, C.POINTER(C.c_int64)] + [_VP] * 8,
+    "pic_get_particles_dev": [_VP, C.c_int, C.c_int64, C.POINTER(C.c_int64)] + [_VP] * 8,
+    "pic_set_fields": [_VP, _P3, _P3],
+    "pic_set_fields_dev": [_VP, _P3, _P3],
+    "pic_get_fields": [_VP, _P3, _P3],
+    "pic_get_fields_dev": [_VP, _P3, _P3],
+    "pic_get_current": [_VP, _P3],
+    "pic_get_current_dev": [_VP, _P3],
+    "pic_step": [_VP, C.c_int],
+    "pic_sync": [_VP],
+    "pic_energy": [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "pic_enable_timing": [_VP, C.c_int],
+    "pic_stage_times": [_VP, C.POINTER(C.c_double * 4)],
+    "pic_launch_count": [_VP, C.POINTER(C.c_int64), C.c_int],
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpicgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libpicgb.so not built: run `python -m paper_1608_01009_gb300.build` "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        lib = C.CDLL(path)
+        for name, args in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name == "pic_last_error" else C.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    """Data pointer of a numpy array (host) or torch tensor (device)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_dev(a) -> bool:
+    return not isinstance(a, np.ndarray)
+
+
+class Simulation:
+    """One PIC context on one GPU.
+
+    Parameters follow pic_grid_desc (include/pic.h).  Fields are (3, nz, ny, nx)
+    arrays, positions physical.  `stream` is a torch.cuda.Stream (default: the
+    current stream of `device`).
+    """
+
+    def __init__(self, n, d, dt, bc=(PERIODIC,) * 3, precision=FP64, supercell=4, sort_interval=0, device=0,
+                 absorb_cells=8, absorb_sigma=0.1, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the PIC library runs only on the GPU")
+        self.lib = load_library()
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        g = GridDesc()
+        for a in range(3):
+            g.n[a] = int(n[a])
+            g.d[a] = float(d[a])
+            g.bc[a] = int(bc[a])
+        g.dt = float(dt)
+        g.absorb_cells = int(absorb_cells)
+        g.absorb_sigma = float(absorb_sigma)
+        g.precision = int(precision)
+        g.supercell = int(supercell)
+        g.sort_interval = int(sort_interval)
+        g.device = int(device)
+        g.stream = stream.cuda_stream
+        self.desc = g
+        self.n, self.d, self.dt = tuple(int(v) for v in n), tuple(float(v) for v in d), float(dt)
+        self.precision = precision
+        self.ctx = _VP()
+        rc = self.lib.pic_create(C.byref(g), C.byref(self.ctx))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_create failed (see stderr)")
+        self.nspecies = 0
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, rc):
+        if rc != PIC_OK:
+            raise PicError(rc, self.lib.pic_last_error(self.ctx).decode())
+
+    def close(self):
+        if self.ctx:
+            self.lib.pic_destroy(self.ctx)
+            self.ctx = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @classmethod
+    def from_workload(cls, wl, precision=FP64, supercell=4, sort_interval=0, device=0, stream=None):
+        sim = cls(wl.n, wl.d, wl.dt, wl.bc, precision, supercell, sort_interval, device, wl.absorb_cells,
+                  wl.absorb_sigma, stream)
+        sim.set_fields(wl.E, wl.B)
+        for sp in wl.species:
+            sim.add_species(sp.q, sp.m, *sp.arrays())
+        return sim
+
+    # ------------------------------------------------------------------ particles
+    def add_species(self, q, m, x, y, z, ux, uy, uz, w) -> int:
+        arrs = [x, y, z, ux, uy, uz, w]
+        dev = _is_dev(x)
+        if not dev:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        else:
+            arrs = [a.contiguous().to(self.torch.float64) for a in arrs]
+        n = int(arrs[0].shape[0])
+        sid = C.c_int(-1)
+        sd = SpeciesDesc(float(q), float(m))
+        f = self.lib.pic_add_species_dev if dev else self.lib.pic_add_species
+        self._check(f(self.ctx, C.byref(sd), n, *[_ptr(a) for a in arrs], C.byref(sid)))
+        if dev:
+            self.stream.synchronize()
+        self.nspecies += 1
+        return sid.value
+
+    def set_particles(self, species, x, y, z, ux, uy, uz, w):
+        arrs = [x, y, z, ux, uy, uz, w]
+        dev = _is_dev(x)
+        if not dev:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        n = int(arrs[0].shape[0])
+        f = self.lib.pic_set_particles_dev if dev else self.lib.pic_set_particles
+        self._check(f(self.ctx, int(species), n, *[_ptr(a) for a in arrs]))
+
+    def count(self, species=0) -> int:
+        n = C.c_int64()
+        self._check(self.lib.pic_count_particles(self.ctx, int(species), C.byref(n)))
+        return n.value
+
+    def get_particles(self, species=0, device=False):
+        """Active particles: dict id, x, y, z, ux, uy, uz, w (numpy, or torch on the GPU)."""
+        cap = self.count(species)
+        if device:
+            t = self.torch
+            out = {"id": t.empty(cap, dtype=t.int64, device=self.device)}
+            for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+                out[k] = t.empty(cap, dtype=t.float64, device=self.device)
+            f = self.lib.pic_get_particles_dev
+        else:
+            out = {"id": np.empty(cap, np.int64)}
+            for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+                out[k] = np.empty(cap, np.float64)
+            f = self.lib.pic_get_particles
+        n = C.c_int64()
+        self._check(f(self.ctx, int(species), cap, C.byref(n), *[_ptr(out[k]) for k in
+                                                                   ("id", "x", "y", "z", "ux", "uy", "uz", "w")]))
+        return out
+
+    # ------------------------------------------------------------------ fields
+    def _field_ptrs(self, F):
+        return _P3(*[_ptr(F[c]) for c in range(3)])
+
+    def set_fields(self, E, B):
+        dev = _is_dev(E)
+        if not dev:
+            E = np.ascontiguousarray(E, dtype=np.float64)
+            B = np.ascontiguousarray(B, dtype=np.float64)
+        f = self.lib.pic_set_fields_dev if dev else self.lib.pic_set_fields
+        self._check(f(self.ctx, self._field_ptrs(E), self._field_ptrs(B)))
+
+    def get_fields(self, device=False):
+        shape = (3, self.n[2], self.n[1], self.n[0])
+        if device:
+            E = self.torch.empty(shape, dtype=self.torch.float64, device=self.device)
+            B = self.torch.empty_like(E)
+            f = self.lib.pic_get_fields_dev
+        else:
+            E, B = np.empty(shape), np.empty(shape)
+            f = self.lib.pic_get_fields
+        self._check(f(self.ctx, self._field_ptrs(E), self._field_ptrs(B)))
+        return E, B
+
+    def get_current(self, device=False):
+        shape = (3, self.n[2], self.n[1], self.n[0])
+        if device:
+            J = self.torch.empty(shape, dtype=self.torch.float64, device=self.device)
+            f = self.lib.pic_get_current_dev
+        else:
+            J = np.empty(shape)
+            f = self.lib.pic_get_current
+        self._check(f(self.ctx, self._field_ptrs(J)))
+        return J
+
+    # ------------------------------------------------------------------ stepping
+    def step(self, nsteps=1):
+        self._check(self.lib.pic_step(self.ctx, int(nsteps)))
+
+    def sync(self):
+        self._check(self.lib.pic_sync(self.ctx))
+
+    def energy(self):
+        wf, wk = C.c_double(), C.c_double()
+        self._check(self.lib.pic_energy(self.ctx, C.byref(wf), C.byref(wk)))
+        return wf.value, wk.value
+
+    def enable_timing(self, on=True):
+        self._check(self.lib.pic_enable_timing(self.ctx, 1 if on else 0))
+
+    def stage_times(self):
+        out = (C.c_double * 4)()
+        self._check(self.lib.pic_stage_times(self.ctx, C.byref(out)))
+        return dict(push_deposit=out[0], field=out[1], sort=out[2], diagnostics=out[3])
+
+    def launch_count(self, reset=False) -> int:
+        n = C.c_int64()
+        self._check(self.lib.pic_launch_count(self.ctx, C.byref(n), 1 if reset else 0))
+        return n.value
