@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 particle-in-cell hot path.
+
+One benchmark step = one whole PIC time step of the workload: field gather,
+Boris push, move and Villasenor-Buneman deposit of every particle, the Yee
+FDTD update, the energy diagnostics, and (every K steps) the supercell sort.
+
+Default workload (1 GPU): the paper-scale FP64 plasma, 64^3 cells with 50
+electrons per cell (13,107,200 particles, the same particles-per-cell as the
+paper's 40^3 x 50 frozen-plasma benchmark), thermal velocity 0.05c, a 1%
+density perturbation along x, periodic.  Inputs are seeded and synthetic,
+resident in HBM when the timed region starts, and larger than L2 (the FP64
+particle store alone is 839 MB).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+independent replica of the workload (the path is not sharded across GPUs);
+the time is the maximum over ranks and the value counts all ranks' particles.
+--impl reference times the FP64 CPU oracle on this host's cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (FP64 plain vs FP32-mixed), HBM roofline %, adjoint/forward ratio"
+UNIT = "particle-steps/s"
+
+# Algorithmic cost of one particle-step of the fused particle kernel, counted
+# from its arithmetic (FMA = 2 flops; rsqrt and divide = 1 each):
+#   gather 6 trilinear interpolations x 7 lerps x 3 + 3 half-offset adds = 129
+#   Boris push 58, move 16, Villasenor-Buneman (one segment) 57, energy 3.
+FLOPS_PER_PARTICLE = 263
+# Minimum HBM traffic per particle-step of the particle store:
+#   FP64 store: read cell(4) + offset(24) + u(24) + w(8) = 60 B, write cell + offset + u = 52 B.
+#   mixed store: read 4 + 12 + 12 + 4 = 32 B, write 4 + 12 + 12 = 28 B.
+BYTES_PER_PARTICLE = {"fp64": 112, "mixed": 60}
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no measured FP64 peak is provided)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_push.cu", "pic_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1608_01009_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kind):
+    """Per-launch DRAM bytes of the particle kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        r = rec.get(kind)
+        if r and r.get("kernel_sha") == _kernel_hash():
+            return r["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(torch, value, ws):
+    if ws == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload_desc(wl, precision):
+    return ("%s: %dx%dx%d %s, %d e-/cell (%d particles), vth %.2fc%s, %s" % (
+        wl.name, wl.n[0], wl.n[1], wl.n[2], "periodic" if wl.bc == (0, 0, 0) else "bc %s" % (wl.bc,),
+        wl.meta.get("ppc", 0), wl.nparticles, wl.meta.get("vth", 0.0),
+        ", 1% density perturbation" if wl.meta.get("perturb_eps") else "", precision))
+
+
+def time_gpu(torch, pic, wl, precision, steps, warmup, clocks=None, with_timing=True):
+    """Device-timed steps of one simulation; returns a result dict."""
+    prec = pic.FP64 if precision == "fp64" else pic.MIXED
+    sim = pic.Simulation.from_workload(wl, precision=prec, supercell=4)
+    st = sim.stream
+    for _ in range(warmup):
+        sim.step(1)
+    sim.sync()
+    sim.stage_times()  # reset the stage accumulators
+    sim.enable_timing(with_timing)
+    before = sim.stage_times()
+    sim.launch_count(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    sim.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count()
+    after = sim.stage_times()
+    sim.enable_timing(False)
+    sim.sync()
+    wf, wk = sim.energy()
+    npart = wl.nparticles
+    res = dict(ms=ms, npart=npart, launches=launches, wf=wf, wk=wk,
+               stage_ms={k: (after[k] - before[k]) / steps for k in after}, sim=sim)
+    return res
+
+
+def time_e2e(torch, pic, wl, sim, steps):
+    """End to end through the public API with HOST buffers: every step uploads
+    the step's particle and field inputs from pinned host memory
+    (pic_set_particles, pic_set_fields), advances one step and reads the
+    energy diagnostics back (pic_energy)."""
+    import numpy as np
+    sp = wl.species[0]
+    pinned = []
+    for a in sp.arrays():
+        t = torch.empty(a.shape[0], dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = a
+        pinned.append(t.numpy())
+    Ep = torch.empty(wl.E.shape, dtype=torch.float64, pin_memory=True).numpy()
+    Bp = torch.empty(wl.B.shape, dtype=torch.float64, pin_memory=True).numpy()
+    Ep[:] = wl.E
+    Bp[:] = wl.B
+    h2d = sum(a.nbytes for a in pinned) + Ep.nbytes + Bp.nbytes
+    d2h = 16
+    # one untimed pass
+    sim.set_fields(Ep, Bp)
+    sim.set_particles(0, *pinned)
+    sim.step(1)
+    sim.energy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.set_fields(Ep, Bp)
+        sim.set_particles(0, *pinned)
+        sim.step(1)
+        sim.energy()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dict(seconds=dt, npart=wl.nparticles, steps=steps, h2d=h2d, d2h=d2h)
+
+
+def cpu_oracle_rate(wl, nsteps=1, sample_every=1):
+    """The FP64 oracle as it stands (single thread) on the workload state,
+    optionally on every k-th particle; returns (particle-steps/s, particles, seconds)."""
+    import oracle as O
+    ora = O.Oracle.from_workload(wl)
+    if sample_every > 1:
+        ora.species = [s.subset(slice(None, None, sample_every)) for s in ora.species]
+    npart = sum(s.n for s in ora.species)
+    t0 = time.perf_counter()
+    ora.step(nsteps)
+    dt = time.perf_counter() - t0
+    return npart * nsteps / dt, npart, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1608_01009_gb300 import workloads as W
+    wl = W.config(args.workload)
+    every = max(1, wl.nparticles // 400_000)  # ~0.4 M particles per step: about a second of CPU work
+    rates = []
+    total_p, total_s = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        r, npart, dt = cpu_oracle_rate(wl, 1, every)
+        if i >= args.warmup:
+            total_p += npart
+            total_s += dt
+    value = total_p / total_s
+    sample = ("each step: one whole oracle step of the %dx%dx%d grid with every %d-th particle "
+              "(%d particles)" % (wl.n[0], wl.n[1], wl.n[2], every, wl.nparticles // every))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded)", "config": {"workload": _workload_desc(wl, "fp64")},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_gpu(args):
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1608_01009_gb300 import pic, workloads as W
+    # every rank its own replica (different seed): weak scaling, no data-path collective
+    wl = W.config(args.workload, seed=None if ws == 1 else 1236 + 101 * rank)
+    peaks, peak_kind = _peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    if ws > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        r = time_gpu(torch, pic, wl, "fp64", args.steps, args.warmup)
+    ms = _barrier_max(torch, r["ms"], ws)
+    value = r["npart"] * ws * args.steps / (ms / 1e3)
+    push_ms = r["stage_ms"]["push_deposit"]
+    flops = FLOPS_PER_PARTICLE * r["npart"]
+    bytes_ = BYTES_PER_PARTICLE["fp64"] * r["npart"]
+    achieved_tf = flops / (push_ms / 1e3) / 1e12
+    achieved_gbs = bytes_ / (push_ms / 1e3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+           "config": {"workload": _workload_desc(wl, "FP64"), "supercell": 4, "sort_interval": 3,
+                      "l2": "inputs larger than L2 (particle store %.0f MB)" % (64 * r["npart"] / 1e6),
+                      "parallelism": "replicas x%d" % ws if ws > 1 else "single GPU"},
+           "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": _traffic("fp64"),
+                        "kernel": "k_push<double,4> (gather + Boris + move + VB deposit)",
+                        "peak_kind": "nominal FP64 of GB300 (recipe); HBM peak of %s" % peak_kind,
+                        "per_launch_ms": push_ms, "hbm_achieved_gbs": achieved_gbs,
+                        "hbm_frac": achieved_gbs / hbm_peak},
+           "stage_ms_per_step": {k: round(v, 4) for k, v in r["stage_ms"].items()},
+           "gpu_launches": r["launches"], "clocks": clk.summary()}
+    if not args.no_e2e:
+        e2e = time_e2e(torch, pic, wl, r["sim"], max(3, min(args.steps, 10)))
+        sec = _barrier_max(torch, e2e["seconds"], ws)
+        out["e2e"] = {"value": e2e["npart"] * ws * e2e["steps"] / sec, "unit": UNIT,
+                      "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                      "how": "per step: pic_set_fields + pic_set_particles from pinned host buffers, "
+                             "pic_step(1), pic_energy (16 B back)"}
+    r["sim"].close()
+    if not args.no_mixed:
+        wl3 = W.config("c3", seed=None if ws == 1 else 1237 + 101 * rank)
+        with ClockSampler(local) as clk3:
+            r3 = time_gpu(torch, pic, wl3, "mixed", args.steps, args.warmup)
+        ms3 = _barrier_max(torch, r3["ms"], ws)
+        pm = r3["stage_ms"]["push_deposit"]
+        gbs = BYTES_PER_PARTICLE["mixed"] * r3["npart"] / (pm / 1e3) / 1e9
+        out["mixed"] = {"value": r3["npart"] * ws * args.steps / (ms3 / 1e3), "unit": UNIT, "dtype": "f32/f64",
+                        "config": {"workload": _workload_desc(wl3, "mixed FP32/FP64")},
+                        "ms_per_step": ms3 / args.steps,
+                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": gbs / hbm_peak, "traffic": _traffic("mixed"),
+                                     "kernel": "k_push<float,4>", "per_launch_ms": pm},
+                        "stage_ms_per_step": {k: round(v, 4) for k, v in r3["stage_ms"].items()},
+                        "gpu_launches": r3["launches"], "clocks": clk3.summary()}
+        r3["sim"].close()
+    if not args.no_replica:
+        wlr = W.config("r")
+        rr = time_gpu(torch, pic, wlr, "fp64", args.steps, args.warmup, with_timing=False)
+        vr = rr["npart"] * args.steps / (rr["ms"] / 1e3)
+        out["paper_replica"] = {"workload": _workload_desc(wlr, "FP64"), "value": vr, "unit": UNIT,
+                                "paper_knl_value": 3.2e9 / 10.75,
+                                "vs_paper_knl": vr / (3.2e9 / 10.75),
+                                "note": "paper: 40^3 x 50 ppc x 1000 steps in 10.75 s on Xeon Phi 7250 "
+                                        "(Table 6); context, other hardware"}
+        rr["sim"].close()
+    if rank == 0 and not args.no_cpu:
+        rate, npart, dt = cpu_oracle_rate(wl, 1, 1)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "one whole oracle step of the full workload (%d particles, %.1f s)"
+                                         % (npart, dt)}
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-replica", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -44,41 +44,31 @@ __device__ __forceinline__ R tri(const R* __restrict__ F, int i, int j, int k, R
     return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
 }
 
-// Current of a straight segment inside the cell whose J-tile corner is (jx,jy,jz):
-// start a (cell-relative), displacement d (cells).  Edge weights are the line
-// integrals of the two transverse CIC weights: W(s1) W(s2) + sigma dp dr / 12.
-template <class R, int TJ>
-__device__ __forceinline__ void segment(R* Jt, int jx, int jy, int jz, R ax, R ay, R az, R dx, R dy, R dz, R Qx,
-                                        R Qy, R Qz) {
-    constexpr int TJ2 = TJ * TJ, TJ3 = TJ * TJ * TJ;
-    const R h = R(0.5), tw = R(1.0 / 12.0);
-    R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
-    R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
-    int b = (jz * TJ + jy) * TJ + jx;
-    {  // Jx on edges (i+1/2, j+s1, k+s2)
-        R c = dy * dz * tw, q = Qx * dx;
-        R* J = Jt + b;
-        atomicAdd(J, q * fma(oy, oz, c));
-        atomicAdd(J + TJ, q * fma(my, oz, -c));
-        atomicAdd(J + TJ2, q * fma(oy, mz, -c));
-        atomicAdd(J + TJ + TJ2, q * fma(my, mz, c));
-    }
-    {  // Jy on edges (i+s1, j+1/2, k+s2)
-        R c = dx * dz * tw, q = Qy * dy;
-        R* J = Jt + TJ3 + b;
-        atomicAdd(J, q * fma(ox, oz, c));
-        atomicAdd(J + 1, q * fma(mx, oz, -c));
-        atomicAdd(J + TJ2, q * fma(ox, mz, -c));
-        atomicAdd(J + 1 + TJ2, q * fma(mx, mz, c));
-    }
-    {  // Jz on edges (i+s1, j+s2, k+1/2)
-        R c = dx * dy * tw, q = Qz * dz;
-        R* J = Jt + 2 * TJ3 + b;
-        atomicAdd(J, q * fma(ox, oy, c));
-        atomicAdd(J + 1, q * fma(mx, oy, -c));
-        atomicAdd(J + TJ, q * fma(ox, my, -c));
-        atomicAdd(J + 1 + TJ, q * fma(mx, my, c));
-    }
+constexpr unsigned FULL = 0xffffffffu;
+
+// Comparisons of cell offsets on their bit patterns (integer ALU, not the FP64
+// pipe).  Offsets lie in [0,1); end points b = offset + displacement lie in
+// (-1, 2) and are never -0.
+__device__ __forceinline__ bool lt_half(double x) { return __double2hiint(x) < 0x3FE00000; }
+__device__ __forceinline__ bool lt_half(float x) { return __float_as_int(x) < 0x3F000000; }
+__device__ __forceinline__ int cell_shift(double b) {
+    const int h = __double2hiint(b);
+    return h < 0 ? -1 : (h >= 0x3FF00000 ? 1 : 0);
+}
+__device__ __forceinline__ int cell_shift(float b) {
+    const int h = __float_as_int(b);
+    return h < 0 ? -1 : (h >= 0x3F800000 ? 1 : 0);
+}
+
+template <class R>
+__device__ __forceinline__ R below_one();
+template <>
+__device__ __forceinline__ double below_one<double>() {
+    return 0x1.fffffffffffffp-1;
+}
+template <>
+__device__ __forceinline__ float below_one<float>() {
+    return 0x1.fffffep-1f;
 }
 
 template <class R>
@@ -96,80 +86,112 @@ __device__ __forceinline__ void sort3(R& a, R& b, R& c) {
     b = hi;
 }
 
-// Villasenor-Buneman split of a move that leaves its start cell: cut at every
-// face crossed (at most one per axis), pieces in order of the crossing
-// parameter, each piece deposited in the cell that contains its midpoint.
+// Current of one straight segment per lane, inside the cell whose J-tile
+// corner index is `key` (-1: nothing to deposit): start a (cell-relative) and
+// displacement d, in cells.  The 12 edge values are the line integrals of the
+// two transverse CIC weights, Q d_c [W(s1) W(s2) + sigma d_p d_r / 12]
+// (Villasenor-Buneman).  Lanes are ordered by cell, so runs of lanes with the
+// same key are first summed by a segmented warp scan; the last lane of each
+// run adds the run's 12 totals to the shared J tile.
 template <class R, int TJ>
-__device__ __noinline__ void deposit_split(R* Jt, int jx, int jy, int jz, R ax, R ay, R az, R dx, R dy, R dz, R Qx,
-                                           R Qy, R Qz) {
-    R bx = ax + dx, by = ay + dy, bz = az + dz;
-    R t1 = (bx < R(0) || bx >= R(1)) ? ((bx >= R(1) ? R(1) : R(0)) - ax) / dx : R(1);
-    R t2 = (by < R(0) || by >= R(1)) ? ((by >= R(1) ? R(1) : R(0)) - ay) / dy : R(1);
-    R t3 = (bz < R(0) || bz >= R(1)) ? ((bz >= R(1) ? R(1) : R(0)) - az) / dz : R(1);
-    sort3(t1, t2, t3);
-    R ts[5] = {R(0), t1, t2, t3, R(1)};
+__device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy,
+                                                R Qz) {
+    constexpr int TJ2 = TJ * TJ, TJ3 = TJ * TJ * TJ;
+    const R h = R(0.5), tw = R(1.0 / 12.0);
+    const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
+    const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
+    R v[12];
+    {  // Jx on edges (i+1/2, j+s1, k+s2)
+        const R q = Qx * dx, qc = q * (dy * dz * tw), qo = q * oy, qm = q * my;
+        v[0] = fma(qo, oz, qc);
+        v[1] = fma(qm, oz, -qc);
+        v[2] = fma(qo, mz, -qc);
+        v[3] = fma(qm, mz, qc);
+    }
+    {  // Jy on edges (i+s1, j+1/2, k+s2)
+        const R q = Qy * dy, qc = q * (dx * dz * tw), qo = q * ox, qm = q * mx;
+        v[4] = fma(qo, oz, qc);
+        v[5] = fma(qm, oz, -qc);
+        v[6] = fma(qo, mz, -qc);
+        v[7] = fma(qm, mz, qc);
+    }
+    {  // Jz on edges (i+s1, j+s2, k+1/2)
+        const R q = Qz * dz, qc = q * (dx * dy * tw), qo = q * ox, qm = q * mx;
+        v[8] = fma(qo, oy, qc);
+        v[9] = fma(qm, oy, -qc);
+        v[10] = fma(qo, my, -qc);
+        v[11] = fma(qm, my, qc);
+    }
+    const int lane = threadIdx.x & 31;
+    const int kprev = __shfl_up_sync(FULL, key, 1);
+    const int knext = __shfl_down_sync(FULL, key, 1);
+    const bool head = lane == 0 || kprev != key;
+    const bool tail = lane == 31 || knext != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const int start = 31 - __clz(heads & (FULL >> (31 - lane)));
+    const int longest = __reduce_max_sync(FULL, (unsigned)(lane - start + 1));
+    for (int dd = 1; dd < longest; dd <<= 1) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        R ta = ts[s], tb = ts[s + 1];
-        if (!(tb > ta)) continue;
-        R pax = fma(ta, dx, ax), pay = fma(ta, dy, ay), paz = fma(ta, dz, az);
-        R pbx = fma(tb, dx, ax), pby = fma(tb, dy, ay), pbz = fma(tb, dz, az);
-        R mx = R(0.5) * (pax + pbx), my = R(0.5) * (pay + pby), mz = R(0.5) * (paz + pbz);
-        int ox = mx < R(0) ? -1 : (mx >= R(1) ? 1 : 0);
-        int oy = my < R(0) ? -1 : (my >= R(1) ? 1 : 0);
-        int oz = mz < R(0) ? -1 : (mz >= R(1) ? 1 : 0);
-        segment<R, TJ>(Jt, jx + ox, jy + oy, jz + oz, pax - R(ox), pay - R(oy), paz - R(oz), pbx - pax, pby - pay,
-                       pbz - paz, Qx, Qy, Qz);
+        for (int i = 0; i < 12; ++i) {
+            const R t = __shfl_up_sync(FULL, v[i], dd);
+            if (lane - dd >= start) v[i] += t;
+        }
+    }
+    if (tail && key >= 0) {
+        R* J = Jt + key;
+        atomicAdd(J, v[0]);
+        atomicAdd(J + TJ, v[1]);
+        atomicAdd(J + TJ2, v[2]);
+        atomicAdd(J + TJ + TJ2, v[3]);
+        J += TJ3;
+        atomicAdd(J, v[4]);
+        atomicAdd(J + 1, v[5]);
+        atomicAdd(J + TJ2, v[6]);
+        atomicAdd(J + 1 + TJ2, v[7]);
+        J += TJ3;
+        atomicAdd(J, v[8]);
+        atomicAdd(J + 1, v[9]);
+        atomicAdd(J + TJ, v[10]);
+        atomicAdd(J + 1 + TJ, v[11]);
     }
 }
 
-template <class R>
-__device__ __forceinline__ R below_one();
-template <>
-__device__ __forceinline__ double below_one<double>() {
-    return 0x1.fffffffffffffp-1;
-}
-template <>
-__device__ __forceinline__ float below_one<float>() {
-    return 0x1.fffffep-1f;
-}
-
-// New cell index along one axis after a displacement whose end point in the
-// start-cell frame is b: shift in {-1,0,1}, new offset in [0,1).
-template <class R>
-__device__ __forceinline__ int shift_of(R b, R& off) {
-    int s = b >= R(1) ? 1 : (b < R(0) ? -1 : 0);
-    R o = b - R(s);
-    off = o < below_one<R>() ? o : below_one<R>();
-    return s;
-}
-
+// One particle per lane; all 32 lanes of the warp call it (lanes without a
+// particle pass valid = false).  Returns w (gamma - 1) of the new state.
 template <class R, int S>
-__device__ __forceinline__ double push_one(const R* __restrict__ F, R* Jt, const PStore<R>& ps, int p,
-                                           const PushParams& pp, int c0x, int c0y, int c0z, int* err) {
+__device__ __forceinline__ R push_lane(const R* __restrict__ F, R* Jt, const PStore<R>& ps, int p, bool valid,
+                                       const PushParams& pp, int c0x, int c0y, int c0z, int* err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
     const GridDev& g = pp.g;
-    int cp = ps.cell[p];
-    if (cp < 0) return 0.0;  // deactivated (left through an absorbing boundary)
+    const int cp = valid ? ps.cell[p] : INACTIVE;
+    bool act = cp >= 0;  // negative: no particle, or deactivated at an absorbing boundary
     int gx = cell_x(cp), gy = cell_y(cp), gz = cell_z(cp);
     // cell relative to the supercell origin: the periodic image next to the tile
     int lx = gx - c0x, ly = gy - c0y, lz = gz - c0z;
     if (lx < -1) lx += g.n[0]; else if (lx > S) lx -= g.n[0];
     if (ly < -1) ly += g.n[1]; else if (ly > S) ly -= g.n[1];
     if (lz < -1) lz += g.n[2]; else if (lz > S) lz -= g.n[2];
-    if ((unsigned)(lx + 1) > (unsigned)(S + 1) || (unsigned)(ly + 1) > (unsigned)(S + 1) ||
-        (unsigned)(lz + 1) > (unsigned)(S + 1)) {
+    if (act && ((unsigned)(lx + 1) > (unsigned)(S + 1) || (unsigned)(ly + 1) > (unsigned)(S + 1) ||
+                (unsigned)(lz + 1) > (unsigned)(S + 1))) {
         atomicOr(err, ERRBIT_DRIFT);
-        return 0.0;
+        act = false;
     }
-    R fx = ps.off[0][p], fy = ps.off[1][p], fz = ps.off[2][p];
-    R ux = ps.u[0][p], uy = ps.u[1][p], uz = ps.u[2][p];
-    const R w = ps.w[p];
+    if (!act) lx = ly = lz = 0;
+    R fx = R(0.25), fy = R(0.25), fz = R(0.25), ux = R(0), uy = R(0), uz = R(0), w = R(0);
+    if (act) {
+        fx = ps.off[0][p];
+        fy = ps.off[1][p];
+        fz = ps.off[2][p];
+        ux = ps.u[0][p];
+        uy = ps.u[1][p];
+        uz = ps.u[2][p];
+        w = ps.w[p];
+    }
 
     // ---- gather: each component from its own staggered lattice (tile origin = cell c0-2)
     const int tx = lx + 2, ty = ly + 2, tz = lz + 2;
     const R hf = R(0.5);
-    const bool sxb = fx < hf, syb = fy < hf, szb = fz < hf;
+    const bool sxb = lt_half(fx), syb = lt_half(fy), szb = lt_half(fz);
     const int hx = sxb ? tx - 1 : tx, hy = syb ? ty - 1 : ty, hz = szb ? tz - 1 : tz;
     const R gxf = fx + (sxb ? hf : -hf), gyf = fy + (syb ? hf : -hf), gzf = fz + (szb ? hf : -hf);
     const R Ex = tri<R, T>(F + 0 * T3, hx, ty, tz, gxf, fy, fz);
@@ -181,14 +203,14 @@ __device__ __forceinline__ double push_one(const R* __restrict__ F, R* Jt, const
 
     // ---- Boris: half electric kick, rotation, half electric kick
     const R h = R(pp.qdt2m);
-    R umx = fma(h, Ex, ux), umy = fma(h, Ey, uy), umz = fma(h, Ez, uz);
-    R hg = h * rsqrt(fma(umx, umx, fma(umy, umy, fma(umz, umz, R(1)))));
-    R tbx = hg * Bx, tby = hg * By, tbz = hg * Bz;
-    R sf = R(2) / (R(1) + fma(tbx, tbx, fma(tby, tby, tbz * tbz)));
-    R sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
-    R upx = fma(umy, tbz, fma(-umz, tby, umx));
-    R upy = fma(umz, tbx, fma(-umx, tbz, umy));
-    R upz = fma(umx, tby, fma(-umy, tbx, umz));
+    const R umx = fma(h, Ex, ux), umy = fma(h, Ey, uy), umz = fma(h, Ez, uz);
+    const R hg = h * rsqrt(fma(umx, umx, fma(umy, umy, fma(umz, umz, R(1)))));
+    const R tbx = hg * Bx, tby = hg * By, tbz = hg * Bz;
+    const R sf = R(2) / (R(1) + fma(tbx, tbx, fma(tby, tby, tbz * tbz)));
+    const R sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
+    const R upx = fma(umy, tbz, fma(-umz, tby, umx));
+    const R upy = fma(umz, tbx, fma(-umx, tbz, umy));
+    const R upz = fma(umx, tby, fma(-umy, tbx, umz));
     ux = fma(h, Ex, fma(upy, sbz, fma(-upz, sby, umx)));
     uy = fma(h, Ey, fma(upz, sbx, fma(-upx, sbz, umy)));
     uz = fma(h, Ez, fma(upx, sby, fma(-upy, sbx, umz)));
@@ -197,29 +219,55 @@ __device__ __forceinline__ double push_one(const R* __restrict__ F, R* Jt, const
     const R u2p1 = fma(ux, ux, fma(uy, uy, fma(uz, uz, R(1))));
     const R gi = rsqrt(u2p1);
     const R dx = ux * (gi * R(pp.dtd[0])), dy = uy * (gi * R(pp.dtd[1])), dz = uz * (gi * R(pp.dtd[2]));
-    const R bxr = fx + dx, byr = fy + dy, bzr = fz + dz;
-
-    // ---- new cell and offset; the end cell must stay inside the tiles' slack
-    R nfx, nfy, nfz;
-    const int sx = shift_of(bxr, nfx), sy = shift_of(byr, nfy), sz = shift_of(bzr, nfz);
-    if ((unsigned)(lx + sx + 1) > (unsigned)(S + 1) || (unsigned)(ly + sy + 1) > (unsigned)(S + 1) ||
-        (unsigned)(lz + sz + 1) > (unsigned)(S + 1)) {
+    const R bx = fx + dx, by = fy + dy, bz = fz + dz;  // end point in the start cell's frame
+    const int sx = cell_shift(bx), sy = cell_shift(by), sz = cell_shift(bz);
+    if (act && ((unsigned)(lx + sx + 1) > (unsigned)(S + 1) || (unsigned)(ly + sy + 1) > (unsigned)(S + 1) ||
+                (unsigned)(lz + sz + 1) > (unsigned)(S + 1))) {
         // cannot happen while K * max(dt/d) < 1; record it, drop the particle, touch no tile
         atomicOr(err, ERRBIT_DRIFT);
         ps.cell[p] = INACTIVE | cp;
-        return 0.0;
+        act = false;
     }
 
     // ---- Villasenor-Buneman deposit into the shared J tile (tile origin = cell c0-1)
-    if (w != R(0)) {
-        const R Qx = R(pp.cq[0]) * w, Qy = R(pp.cq[1]) * w, Qz = R(pp.cq[2]) * w;
-        const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
-        if ((sx | sy | sz) == 0)
-            segment<R, TJ>(Jt, jx, jy, jz, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
-        else
-            deposit_split<R, TJ>(Jt, jx, jy, jz, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+    const bool dep = act && w != R(0);
+    const R wq = dep ? w : R(0);
+    const R Qx = R(pp.cq[0]) * wq, Qy = R(pp.cq[1]) * wq, Qz = R(pp.cq[2]) * wq;
+    const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
+    const int nseg = 1 + (sx != 0) + (sy != 0) + (sz != 0);
+    if (!__any_sync(FULL, dep && nseg > 1)) {
+        // no lane leaves its cell: one segment each
+        deposit_segment<R, TJ>(Jt, dep ? (jz * TJ + jy) * TJ + jx : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+    } else {
+        // cut each move at the faces it crosses, pieces in order of the crossing
+        // parameter t; piece s spans [t_s, t_{s+1}] and lies in the cell that
+        // holds its midpoint
+        R t1 = R(1), t2 = R(1), t3 = R(1);
+        if (sx) t1 = (R(sx > 0 ? 1 : 0) - fx) / dx;
+        if (sy) t2 = (R(sy > 0 ? 1 : 0) - fy) / dy;
+        if (sz) t3 = (R(sz > 0 ? 1 : 0) - fz) / dz;
+        sort3(t1, t2, t3);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (!__any_sync(FULL, dep && s < nseg)) break;
+            const R ta = s == 0 ? R(0) : (s == 1 ? t1 : (s == 2 ? t2 : t3));
+            const R tb = s == 0 ? t1 : (s == 1 ? t2 : (s == 2 ? t3 : R(1)));
+            const bool on = dep && s < nseg && tb > ta;
+            const R pax = fma(ta, dx, fx), pay = fma(ta, dy, fy), paz = fma(ta, dz, fz);
+            const R dt = tb - ta;
+            const R ddx = dt * dx, ddy = dt * dy, ddz = dt * dz;
+            const int ox = cell_shift(fma(R(0.5), ddx, pax)), oy = cell_shift(fma(R(0.5), ddy, pay)),
+                      oz = cell_shift(fma(R(0.5), ddz, paz));
+            deposit_segment<R, TJ>(Jt, on ? ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox) : -1, pax - R(ox),
+                                   pay - R(oy), paz - R(oz), ddx, ddy, ddz, Qx, Qy, Qz);
+        }
     }
+    if (!act) return R(0);
 
+    // ---- new cell and offset
+    const R nfx = sx ? fmin(bx - R(sx), below_one<R>()) : bx;
+    const R nfy = sy ? fmin(by - R(sy), below_one<R>()) : by;
+    const R nfz = sz ? fmin(bz - R(sz), below_one<R>()) : bz;
     int ng[3] = {gx + sx, gy + sy, gz + sz};
     bool gone = false;
 #pragma unroll
@@ -237,7 +285,7 @@ __device__ __forceinline__ double push_one(const R* __restrict__ F, R* Jt, const
     ps.u[1][p] = uy;
     ps.u[2][p] = uz;
     // kinetic energy of the new state: w (gamma - 1), gamma = (1 + u^2) / sqrt(1 + u^2)
-    return gone ? 0.0 : (double)w * (double)fma(u2p1, gi, R(-1));
+    return gone ? R(0) : w * fma(u2p1, gi, R(-1));
 }
 
 template <class R, int S, int NT>
@@ -252,6 +300,7 @@ __global__ void __launch_bounds__(NT) k_push(const __grid_constant__ CUtensorMap
     __shared__ uint64_t bar;
     __shared__ double red[NT / 32];
     const GridDev& g = pp.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -278,8 +327,12 @@ __global__ void __launch_bounds__(NT) k_push(const __grid_constant__ CUtensorMap
         }
         phase ^= 1u;
         const int end = ch.start + ch.count;
-        for (int p = ch.start + threadIdx.x; p < end; p += NT)
-            ek += push_one<R, S>(F, Jt, ps, p, pp, c0x, c0y, c0z, err);
+        R ek_chunk = R(0);  // at most CHUNK / NT particles per lane
+        for (int base = ch.start + warp * 32; base < end; base += NT) {
+            const int p = base + lane;
+            ek_chunk += push_lane<R, S>(F, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err);
+        }
+        ek += (double)ek_chunk;
         __syncthreads();
         // merge: J tile cell t is domain cell c0 - 1 + t, padded index c0 + 1 + t
         for (int i = threadIdx.x; i < 3 * TJ3; i += NT) {

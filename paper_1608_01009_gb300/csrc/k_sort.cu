@@ -2,27 +2,39 @@
 //
 // arXiv:1608.01009 Sec. 3 stores particles per cell and Sec. 4.3 processes them
 // by supercells of S^3 cells.  On the GPU the store is one structure of arrays
-// kept ordered by supercell ("bins"); every K steps (K * max(dt/d) < 1, so a
-// particle never leaves its supercell's one-cell slack in between) it is
-// re-binned by a counting sort (the order inside a bin is unspecified):
-//   k_sort_count   : key = supercell of each active particle, histogram with
-//                    warp-aggregated atomics (one atomic per distinct key per warp)
-//   k_sort_scan    : one CTA: exclusive scan of the histogram -> bin starts and
-//                    scatter cursors, new particle count, and the chunk table the
-//                    particle kernel walks (each bin cut into near-equal chunks
-//                    of at most CHUNK particles)
-//   k_sort_scatter : every active particle copied to its slot in the other
-//                    buffer; deactivated particles are dropped (compaction)
+// ordered by supercell and, inside a supercell, by cell.  Every K steps
+// (K * max(dt/d) < 1, so a particle never leaves its supercell's one-cell slack
+// in between) it is re-sorted by a counting sort over cell keys
+//   key = supercell * S^3 + local cell,
+// so that each supercell is a contiguous run of cell runs (the particle kernel
+// relies on the cell order: warp lanes that share a cell share their gather
+// loads and sum their currents before the shared-memory atomics):
+//   k_sort_count  : histogram of keys, warp-aggregated atomics (one atomic per
+//                   distinct key per warp); deactivated particles get no key
+//   k_scan_tiles  : per tile of SCAN_TILE keys, exclusive prefix into cursor[]
+//                   and the tile total
+//   k_scan_top    : one CTA: scan of the tile totals, new particle count, the
+//                   supercell bin starts and the chunk table the particle
+//                   kernel walks (each bin cut into near-equal chunks of at
+//                   most CHUNK particles)
+//   k_scan_add    : cursor[] += tile offset; the histogram is cleared
+//   k_sort_scatter: every active particle copied to its slot in the other
+//                   buffer (order inside a cell unspecified); deactivated
+//                   particles are dropped (compaction)
 #include "pic_internal.cuh"
 
 namespace picgb {
 
 constexpr int SORT_NT = 256;
 constexpr int SCAN_NT = 1024;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_NT * SCAN_PER;  // keys per tile; a multiple of every S^3
 
-__device__ __forceinline__ int bin_of(const GridDev& g, int cp) {
-    const int bx = cell_x(cp) / g.S, by = cell_y(cp) / g.S, bz = cell_z(cp) / g.S;
-    return bx + g.nsc[0] * (by + g.nsc[1] * bz);
+__device__ __forceinline__ int cell_key(const GridDev& g, int cp) {
+    const int S = g.S;
+    const int ix = cell_x(cp), iy = cell_y(cp), iz = cell_z(cp);
+    const int sc = ix / S + g.nsc[0] * (iy / S + g.nsc[1] * (iz / S));
+    return (sc * S + iz % S) * S * S + (iy % S) * S + ix % S;
 }
 
 template <class R>
@@ -36,65 +48,131 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long
         int key = -1;
         if (p < N) {
             const int cp = ps.cell[p];
-            key = cp < 0 ? -1 : bin_of(g, cp);
+            key = cp < 0 ? -1 : cell_key(g, cp);
             keys[p] = key;
         }
         warp_agg_slot(counts, key);
     }
 }
 
-__global__ void __launch_bounds__(SCAN_NT) k_sort_scan(int* __restrict__ counts, int nbins, int* __restrict__ bin_start,
-                                                      int* __restrict__ cursor, long long* __restrict__ n_next,
-                                                      Chunk* __restrict__ chunks, int* __restrict__ nchunks) {
-    __shared__ long long s_cnt[SCAN_NT];
-    __shared__ int s_nch[SCAN_NT];
-    const int per = (nbins + SCAN_NT - 1) / SCAN_NT;
-    const int b0 = threadIdx.x * per, b1 = min(nbins, b0 + per);
-    long long cnt = 0;
+// Exclusive block scan of one value per thread (SCAN_NT threads).
+__device__ int block_exclusive_scan(int v, int* s, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = s[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        s[lane] = t;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? s[w - 1] : 0) + x - v;
+    *total = s[31];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_tiles(const int* __restrict__ counts, long long nkeys,
+                                                       int* __restrict__ cursor, int* __restrict__ tile_sum) {
+    __shared__ int s[32];
+    const long long k0 = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_PER;
+    int c[SCAN_PER];
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        c[i] = k0 + i < nkeys ? counts[k0 + i] : 0;
+        sum += c[i];
+    }
+    int total;
+    int run = block_exclusive_scan(sum, s, &total);
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        if (k0 + i < nkeys) cursor[k0 + i] = run;
+        run += c[i];
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// One CTA: tile offsets, bin starts, chunk table, new particle count.
+__global__ void __launch_bounds__(SCAN_NT) k_scan_top(int* __restrict__ tile_sum, int ntiles,
+                                                     const int* __restrict__ cursor, long long nkeys, int keys_per_bin,
+                                                     int nbins, int* __restrict__ bin_start, long long* __restrict__ n_next,
+                                                     Chunk* __restrict__ chunks, int* __restrict__ nchunks) {
+    __shared__ int s[32];
+    __shared__ int s_total;
+    // exclusive scan of the tile totals, in place (tiles <= SCAN_NT * per)
+    const int per_t = (ntiles + SCAN_NT - 1) / SCAN_NT;
+    const int t0 = threadIdx.x * per_t, t1 = min(ntiles, t0 + per_t);
+    int sum = 0;
+    for (int t = t0; t < t1; ++t) sum += tile_sum[t];
+    int total;
+    int run = block_exclusive_scan(sum, s, &total);
+    for (int t = t0; t < t1; ++t) {
+        const int v = tile_sum[t];
+        tile_sum[t] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) s_total = total;
+    __syncthreads();
+    // bin starts = key prefix at each bin's first key
+    const int per_b = (nbins + SCAN_NT - 1) / SCAN_NT;
+    const int b0 = threadIdx.x * per_b, b1 = min(nbins, b0 + per_b);
+    auto start_of = [&](int b) -> int {
+        if (b >= nbins) return s_total;
+        const long long k = (long long)b * keys_per_bin;
+        return tile_sum[k / SCAN_TILE] + cursor[k];
+    };
     int nch = 0;
     for (int b = b0; b < b1; ++b) {
-        const int c = counts[b];
-        cnt += c;
-        nch += (c + CHUNK - 1) / CHUNK;
+        const int cnt = start_of(b + 1) - start_of(b);
+        nch += (cnt + CHUNK - 1) / CHUNK;
     }
-    s_cnt[threadIdx.x] = cnt;
-    s_nch[threadIdx.x] = nch;
-    __syncthreads();
-    // inclusive Hillis-Steele scan over the per-thread sums
-    for (int off = 1; off < SCAN_NT; off <<= 1) {
-        long long vc = threadIdx.x >= off ? s_cnt[threadIdx.x - off] : 0;
-        int vn = threadIdx.x >= off ? s_nch[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_cnt[threadIdx.x] += vc;
-        s_nch[threadIdx.x] += vn;
-        __syncthreads();
-    }
-    long long start = s_cnt[threadIdx.x] - cnt;
-    int ch = s_nch[threadIdx.x] - nch;
+    int nch_total;
+    int ch = block_exclusive_scan(nch, s, &nch_total);
     for (int b = b0; b < b1; ++b) {
-        const int c = counts[b];
-        bin_start[b] = (int)start;
-        cursor[b] = (int)start;
-        const int k = (c + CHUNK - 1) / CHUNK;
+        const int st = start_of(b);
+        const int cnt = start_of(b + 1) - st;
+        bin_start[b] = st;
+        const int k = (cnt + CHUNK - 1) / CHUNK;
         if (k > 0) {
-            const int base = c / k, rem = c % k;
+            const int base = cnt / k, rem = cnt % k;
             for (int q = 0; q < k; ++q) {
                 Chunk e;
                 e.sc = b;
-                e.start = (int)start + q * base + min(q, rem);
+                e.start = st + q * base + min(q, rem);
                 e.count = base + (q < rem ? 1 : 0);
                 e.pad = 0;
                 chunks[ch + q] = e;
             }
         }
         ch += k;
-        start += c;
-        counts[b] = 0;  // ready for the next sort
     }
-    if (threadIdx.x == SCAN_NT - 1) {
-        bin_start[nbins] = (int)s_cnt[SCAN_NT - 1];
-        *n_next = s_cnt[SCAN_NT - 1];
-        *nchunks = s_nch[SCAN_NT - 1];
+    if (threadIdx.x == 0) {
+        bin_start[nbins] = s_total;
+        *n_next = s_total;
+        *nchunks = nch_total;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_NT) k_scan_add(int* __restrict__ counts, long long nkeys,
+                                                     int* __restrict__ cursor, const int* __restrict__ tile_off) {
+    const long long k0 = (long long)blockIdx.x * SCAN_TILE + threadIdx.x;
+    const int off = tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        const long long k = k0 + (long long)i * SCAN_NT;
+        if (k < nkeys) {
+            cursor[k] += off;
+            counts[k] = 0;  // ready for the next sort
+        }
     }
 }
 
@@ -122,19 +200,27 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter(PStore<R> src, PStore<
 
 int sort_grid(int nsm) { return nsm * 8; }
 
+long long sort_tiles(long long nkeys) { return (nkeys + SCAN_TILE - 1) / SCAN_TILE; }
+
 template <class R>
 cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> src, PStore<R> dst,
-                        const long long* n_cur, long long* n_next, int* keys, int* counts, int* cursor, int* bin_start,
-                        Chunk* chunks, int* nchunks) {
+                        const long long* n_cur, long long* n_next, int* keys, int* counts, int* cursor, int* tile_sum,
+                        int* bin_start, Chunk* chunks, int* nchunks) {
+    const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int ntiles = (int)sort_tiles(nkeys);
+    const int kpb = g.S * g.S * g.S;
     k_sort_count<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, n_cur, g, keys, counts);
-    k_sort_scan<<<1, SCAN_NT, 0, st>>>(counts, g.nbins, bin_start, cursor, n_next, chunks, nchunks);
+    k_scan_tiles<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum);
+    k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, ntiles, cursor, nkeys, kpb, g.nbins, bin_start, n_next, chunks,
+                                      nchunks);
+    k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum);
     k_sort_scatter<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, dst, n_cur, keys, cursor);
     return cudaGetLastError();
 }
 
 template cudaError_t sort_launch<double>(cudaStream_t, int, const GridDev&, PStore<double>, PStore<double>,
-                                         const long long*, long long*, int*, int*, int*, int*, Chunk*, int*);
+                                         const long long*, long long*, int*, int*, int*, int*, int*, Chunk*, int*);
 template cudaError_t sort_launch<float>(cudaStream_t, int, const GridDev&, PStore<float>, PStore<float>,
-                                        const long long*, long long*, int*, int*, int*, int*, Chunk*, int*);
+                                        const long long*, long long*, int*, int*, int*, int*, int*, Chunk*, int*);
 
 }  // namespace picgb

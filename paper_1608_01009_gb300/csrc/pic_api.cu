@@ -21,7 +21,8 @@ cudaError_t field_energy_launch(cudaStream_t, const double*, const GridDev&, dou
 int fdtd_blocks(const GridDev&);
 template <class R>
 cudaError_t sort_launch(cudaStream_t, int, const GridDev&, PStore<R>, PStore<R>, const long long*, long long*, int*,
-                        int*, int*, int*, Chunk*, int*);
+                        int*, int*, int*, int*, Chunk*, int*);
+long long sort_tiles(long long nkeys);
 template <class R>
 cudaError_t load_launch(cudaStream_t, long long, const double* const*, const PStore<R>&, const GridDev&);
 template <class R>
@@ -55,6 +56,7 @@ struct Species {
     Chunk* d_chunks = nullptr;
     int* d_nchunks = nullptr;
     double* d_ek = nullptr;        // kinetic-energy partials of the last push (push_grid entries)
+    double* d_stage = nullptr;     // 7 x cap FP64 staging area for host uploads (allocated on first use)
     std::vector<void*> allocs;
 };
 
@@ -80,8 +82,9 @@ struct pic_ctx {
     int* d_err = nullptr;
     int* d_keys = nullptr;
     long long keys_cap = 0;
-    int* d_counts = nullptr;
-    int* d_cursor = nullptr;
+    int* d_counts = nullptr;    // per-cell histogram of the sort (ncell)
+    int* d_cursor = nullptr;    // per-cell scatter cursor (ncell)
+    int* d_tile_sum = nullptr;  // per-tile totals of the sort's scan
     int* d_counter = nullptr;
     double* d_wf = nullptr;     // field-energy partials (fdtd blocks)
     double* d_ekall = nullptr;  // kinetic partials, contiguous over species
@@ -233,9 +236,9 @@ template <class R>
 int sort_species(pic_ctx* c, Species& s) {
     Store<R>& st = store_of<R>(s);
     cudaError_t e = sort_launch<R>(c->st, c->nsm, c->g, st.a(), st.b(), s.d_n, s.d_n + 1, c->d_keys, c->d_counts,
-                                   c->d_cursor, s.d_bin_start, s.d_chunks, s.d_nchunks);
+                                   c->d_cursor, c->d_tile_sum, s.d_bin_start, s.d_chunks, s.d_nchunks);
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "sort launch: %s", cudaGetErrorString(e));
-    c->launches += 3;
+    c->launches += 5;
     st.cur ^= 1;
     CUDA_TRY(c, cudaMemcpyAsync(s.d_n, s.d_n + 1, sizeof(long long), cudaMemcpyDeviceToDevice, c->st));
     return PIC_OK;
@@ -324,18 +327,12 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
     int r = ensure_keys(c, kmax > s.cap ? kmax : s.cap);
     if (r) return r;
     // stage FP64 inputs on the device when they come from the host
-    std::vector<double*> tmp;
     const double* dsrc[7];
     if (!device && n > 0) {
+        if (!s.d_stage && (r = dalloc(c, s.allocs, &s.d_stage, (size_t)7 * s.cap))) return r;
         for (int k = 0; k < 7; ++k) {
-            double* d = nullptr;
-            if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) {
-                cudaGetLastError();
-                for (double* t : tmp) cudaFree(t);
-                return fail(c, PIC_ERR_OOM, "staging buffer");
-            }
-            tmp.push_back(d);
-            cudaMemcpyAsync(d, src[k], n * sizeof(double), cudaMemcpyHostToDevice, c->st);
+            double* d = s.d_stage + (size_t)k * s.cap;
+            CUDA_TRY(c, cudaMemcpyAsync(d, src[k], n * sizeof(double), cudaMemcpyHostToDevice, c->st));
             dsrc[k] = d;
         }
     } else {
@@ -350,10 +347,6 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
     // bin the new particles; the other species are re-sorted too, so that every
     // species starts the next sort interval together
     r = sort_all(c);
-    if (!tmp.empty()) {
-        cudaStreamSynchronize(c->st);
-        for (double* t : tmp) cudaFree(t);
-    }
     c->energy_fresh = false;
     return r;
 }
@@ -578,8 +571,9 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
     if ((r = dalloc(c, c->allocs, &c->Jlast, 3 * ncell))) return bail(r);
     if (c->mixed && (r = dalloc(c, c->allocs, &c->EB32, 6 * g.P))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_err, 1))) return bail(r);
-    if ((r = dalloc(c, c->allocs, &c->d_counts, g.nbins))) return bail(r);
-    if ((r = dalloc(c, c->allocs, &c->d_cursor, g.nbins))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_counts, ncell))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_cursor, ncell))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_tile_sum, sort_tiles(ncell)))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_counter, 1))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_wf, fdtd_blocks(g)))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_energy, 2))) return bail(r);
@@ -588,7 +582,7 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
     cudaMemsetAsync(c->Jlast, 0, 3 * ncell * sizeof(double), c->st);
     if (c->EB32) cudaMemsetAsync(c->EB32, 0, 6 * g.P * sizeof(float), c->st);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
-    cudaMemsetAsync(c->d_counts, 0, g.nbins * sizeof(int), c->st);
+    cudaMemsetAsync(c->d_counts, 0, ncell * sizeof(int), c->st);
     cudaMemsetAsync(c->d_energy, 0, 2 * sizeof(double), c->st);
     if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) {
         fail(c, PIC_ERR_CUDA, "init: %s", cudaGetErrorString(e));

@@ -180,5 +180,5 @@ def test_status_and_launch_count():
     sim.launch_count(reset=True)
     sim.step(6)
     sim.sync()
-    # per step: 1 push + 3 field + 1 energy; one sort (3 kernels) at the 4th step (K = 3)
-    assert sim.launch_count() == 6 * 5 + 3
+    # per step: 1 push + 3 field + 1 energy; one sort (5 kernels) at the 4th step (K = 3)
+    assert sim.launch_count() == 6 * 5 + 5
