@@ -201,6 +201,30 @@ PIC_API int pic_stage_times(pic_ctx* ctx, double out[4]);
 /* Kernels this context has launched since creation (or the last reset). */
 PIC_API int pic_launch_count(pic_ctx* ctx, int64_t* n, int reset);
 
+/* Field energy W_F = 1/2 dx dy dz sum (E^2 + B^2) of caller-provided fields,
+ * allocating nothing.  The paper has no counterpart: this is a library
+ * facility for callers that cannot allocate device memory -- a host framework
+ * that owns all device memory through its own pool, a process that has
+ * already reserved the whole device, or a latency-critical loop that cannot
+ * take cudaMalloc's implicit device-wide synchronisation.  It needs no
+ * context.
+ *   E[3], B[3]  device arrays in the unpadded layout above (nx*ny*nz doubles)
+ *   n[3], d[3]  cells per axis and cell sizes (host arrays)
+ *   wf          device pointer to one double; written when `stream` runs the work
+ *   stream      cudaStream_t (NULL = legacy default stream)
+ * Scratch: the per-block partial sums live in one fixed device array of
+ * 65,536 doubles (512 KiB) that every GPU which loads the library holds until
+ * the process exits, so grids are limited to 16,777,216 cells (256^3); larger
+ * ones return PIC_ERR_ARG with a message on stderr.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (unordered streams)
+ * race.  Each call overwrites every partial it reads, so nothing is cleared
+ * between calls.  Returns PIC_OK once the work is enqueued, PIC_ERR_ARG or
+ * PIC_ERR_CUDA. */
+PIC_API int pic_field_energy_noalloc(const double* const E[3], const double* const B[3], const int32_t n[3],
+                                     const double d[3], double* wf, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

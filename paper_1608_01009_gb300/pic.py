@@ -69,6 +69,7 @@ SIGNATURES = {
     "pic_enable_timing": [_VP, C.c_int],
     "pic_stage_times": [_VP, C.POINTER(C.c_double * 4)],
     "pic_launch_count": [_VP, C.POINTER(C.c_int64), C.c_int],
+    "pic_field_energy_noalloc": [_P3, _P3, C.POINTER(C.c_int32 * 3), C.POINTER(C.c_double * 3), _VP, _VP],
 }
 
 
