@@ -47,7 +47,7 @@ __device__ __forceinline__ double damp1(const GridDev& g, double p, int n) {
     double dist = fmin(p, (double)n - p);
     double L = (double)g.absorb_cells;
     if (g.absorb_cells <= 0 || dist >= L) return 1.0;
-    double r = (L - dist) / L;
+    double r = (L - dist) * g.absorb_rL;
     return 1.0 - g.absorb_sigma * r * r;
 }
 
@@ -83,23 +83,32 @@ __device__ __forceinline__ void store_images(R* A, const GridDev& g, const Img& 
     }
 }
 
-constexpr int FDTD_NT = 256;
+// Launch geometry: blocks of 32 x 8 cells in x,y, one z plane per grid z, so
+// (i,j,k) come from the block and thread indices without integer division.
+constexpr int FDTD_BX = 32, FDTD_BY = 8, FDTD_NT = FDTD_BX * FDTD_BY;
+
+__device__ __forceinline__ bool cell_of_thread(const GridDev& g, int& i, int& j, int& k) {
+    i = blockIdx.x * FDTD_BX + threadIdx.x;
+    j = blockIdx.y * FDTD_BY + threadIdx.y;
+    k = blockIdx.z;
+    return i < g.n[0] && j < g.n[1];
+}
+
+__device__ __forceinline__ int flat_block() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
 __global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, GridDev g, double h, int last,
                                                     float* __restrict__ EB32, double* __restrict__ wf_part) {
     __shared__ double red[FDTD_NT / 32];
-    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
     double e2 = 0.0;
-    if (t < ncell) {
-        const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    int i, j, k;
+    if (cell_of_thread(g, i, j, k)) {
         const long long o = pidx(g, i, j, k);
         const long long sy = g.np[0], sz = (long long)g.np[0] * g.np[1];
         const double* Ex = EB;
         const double* Ey = EB + g.P;
         const double* Ez = EB + 2 * g.P;
         double* B = EB + 3 * g.P;
-        const double rx = 1.0 / g.d[0], ry = 1.0 / g.d[1], rz = 1.0 / g.d[2];
+        const double rx = g.rd[0], ry = g.rd[1], rz = g.rd[2];
         const double ex = Ex[o], ey = Ey[o], ez = Ez[o];
         const double cx = (Ez[o + sy] - ez) * ry - (Ey[o + sz] - ey) * rz;
         const double cy = (Ex[o + sz] - ex) * rz - (Ez[o + 1] - ez) * rx;
@@ -122,42 +131,51 @@ __global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, Gri
     }
     if (last) {
         const double s = block_sum<FDTD_NT>(e2, red);
-        if (threadIdx.x == 0) wf_part[blockIdx.x] = s;
+        if (threadIdx.x == 0 && threadIdx.y == 0) wf_part[flat_block()] = s;
     }
 }
 
 __global__ void __launch_bounds__(FDTD_NT) k_fdtd_e(double* __restrict__ EB, double* __restrict__ J,
                                                     double* __restrict__ Jlast, GridDev g) {
     const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
-    if (t >= ncell) return;
-    const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    int i, j, k;
+    if (!cell_of_thread(g, i, j, k)) return;
+    const long long t = i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
     const long long o = pidx(g, i, j, k);
     const long long sy = g.np[0], sz = (long long)g.np[0] * g.np[1];
-    const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
-    // fold J: sum the cell and its periodic images, zero everything read
-    double jc[3] = {0.0, 0.0, 0.0};
-    for (int c3 = 0; c3 < iz.cnt; ++c3)
-        for (int b3 = 0; b3 < iy.cnt; ++b3)
-            for (int a3 = 0; a3 < ix.cnt; ++a3) {
-                const long long q = pidx(g, ix.idx[a3], iy.idx[b3], iz.idx[c3]);
-                const bool fold = ix.fold[a3] && iy.fold[b3] && iz.fold[c3];
-                for (int c = 0; c < 3; ++c) {
-                    if (fold) jc[c] += J[c * g.P + q];
-                    J[c * g.P + q] = 0.0;
-                }
-            }
-    for (int c = 0; c < 3; ++c) Jlast[c * ncell + t] = jc[c];
     const double* Bx = EB + 3 * g.P;
     const double* By = EB + 4 * g.P;
     const double* Bz = EB + 5 * g.P;
-    const double rx = 1.0 / g.d[0], ry = 1.0 / g.d[1], rz = 1.0 / g.d[2];
+    // every load of the cell first (they are independent), then the ghost fold
     const double bx = Bx[o], by = By[o], bz = Bz[o];
-    const double cx = (bz - Bz[o - sy]) * ry - (by - By[o - sz]) * rz;
-    const double cy = (bx - Bx[o - sz]) * rz - (bz - Bz[o - 1]) * rx;
-    const double cz = (by - By[o - 1]) * rx - (bx - Bx[o - sy]) * ry;
-    double e[3] = {EB[o] + g.dt * (cx - jc[0]), EB[g.P + o] + g.dt * (cy - jc[1]),
-                   EB[2 * g.P + o] + g.dt * (cz - jc[2])};
+    const double bz_y = Bz[o - sy], by_z = By[o - sz], bx_z = Bx[o - sz], bz_x = Bz[o - 1], by_x = By[o - 1],
+                 bx_y = Bx[o - sy];
+    const double e0 = EB[o], e1 = EB[g.P + o], e2 = EB[2 * g.P + o];
+    double jc[3] = {J[o], J[g.P + o], J[2 * g.P + o]};
+    const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
+    if (ix.cnt * iy.cnt * iz.cnt > 1) {
+        // boundary cell: add the periodic ghost images of J, zero every image read
+        for (int c3 = 0; c3 < iz.cnt; ++c3)
+            for (int b3 = 0; b3 < iy.cnt; ++b3)
+                for (int a3 = 0; a3 < ix.cnt; ++a3) {
+                    if ((a3 | b3 | c3) == 0) continue;
+                    const long long q = pidx(g, ix.idx[a3], iy.idx[b3], iz.idx[c3]);
+                    const bool fold = ix.fold[a3] && iy.fold[b3] && iz.fold[c3];
+                    for (int c = 0; c < 3; ++c) {
+                        if (fold) jc[c] += J[c * g.P + q];
+                        J[c * g.P + q] = 0.0;
+                    }
+                }
+    }
+    for (int c = 0; c < 3; ++c) {
+        J[c * g.P + o] = 0.0;
+        Jlast[c * ncell + t] = jc[c];
+    }
+    const double rx = g.rd[0], ry = g.rd[1], rz = g.rd[2];
+    const double cx = (bz - bz_y) * ry - (by - by_z) * rz;
+    const double cy = (bx - bx_z) * rz - (bz - bz_x) * rx;
+    const double cz = (by - by_x) * rx - (bx - bx_y) * ry;
+    double e[3] = {e0 + g.dt * (cx - jc[0]), e1 + g.dt * (cy - jc[1]), e2 + g.dt * (cz - jc[2])};
     if (any_absorbing(g))
         for (int c = 0; c < 3; ++c) e[c] *= damping(g, c, false, i, j, k);
     for (int c = 0; c < 3; ++c) store_images(EB + c * g.P, g, ix, iy, iz, e[c]);
@@ -165,10 +183,8 @@ __global__ void __launch_bounds__(FDTD_NT) k_fdtd_e(double* __restrict__ EB, dou
 
 // Refresh ghosts (and the FP32 copy) from the domain values after E/B are set.
 __global__ void __launch_bounds__(FDTD_NT) k_refresh(double* __restrict__ EB, GridDev g, float* __restrict__ EB32) {
-    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
-    if (t >= ncell) return;
-    const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    int i, j, k;
+    if (!cell_of_thread(g, i, j, k)) return;
     const long long o = pidx(g, i, j, k);
     const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
     for (int c = 0; c < 6; ++c) {
@@ -182,11 +198,9 @@ __global__ void __launch_bounds__(FDTD_NT) k_refresh(double* __restrict__ EB, Gr
 __global__ void __launch_bounds__(FDTD_NT) k_field_energy(const double* __restrict__ EB, GridDev g,
                                                           double* __restrict__ wf_part) {
     __shared__ double red[FDTD_NT / 32];
-    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-    const long long t = (long long)blockIdx.x * FDTD_NT + threadIdx.x;
     double e2 = 0.0;
-    if (t < ncell) {
-        const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    int i, j, k;
+    if (cell_of_thread(g, i, j, k)) {
         const long long o = pidx(g, i, j, k);
         for (int c = 0; c < 6; ++c) {
             const double v = EB[c * g.P + o];
@@ -194,32 +208,36 @@ __global__ void __launch_bounds__(FDTD_NT) k_field_energy(const double* __restri
         }
     }
     const double s = block_sum<FDTD_NT>(e2, red);
-    if (threadIdx.x == 0) wf_part[blockIdx.x] = s;
+    if (threadIdx.x == 0 && threadIdx.y == 0) wf_part[flat_block()] = s;
+}
+
+static dim3 fdtd_grid(const GridDev& g) {
+    return dim3((g.n[0] + FDTD_BX - 1) / FDTD_BX, (g.n[1] + FDTD_BY - 1) / FDTD_BY, g.n[2]);
 }
 
 int fdtd_blocks(const GridDev& g) {
-    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-    return (int)((ncell + FDTD_NT - 1) / FDTD_NT);
+    const dim3 b = fdtd_grid(g);
+    return (int)(b.x * b.y * b.z);
 }
 
 cudaError_t fdtd_b_launch(cudaStream_t st, double* EB, const GridDev& g, double h, int last, float* EB32,
                           double* wf_part) {
-    k_fdtd_b<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, g, h, last, EB32, wf_part);
+    k_fdtd_b<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, g, h, last, EB32, wf_part);
     return cudaGetLastError();
 }
 
 cudaError_t fdtd_e_launch(cudaStream_t st, double* EB, double* J, double* Jlast, const GridDev& g) {
-    k_fdtd_e<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, J, Jlast, g);
+    k_fdtd_e<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, J, Jlast, g);
     return cudaGetLastError();
 }
 
 cudaError_t refresh_launch(cudaStream_t st, double* EB, const GridDev& g, float* EB32) {
-    k_refresh<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, g, EB32);
+    k_refresh<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, g, EB32);
     return cudaGetLastError();
 }
 
 cudaError_t field_energy_launch(cudaStream_t st, const double* EB, const GridDev& g, double* wf_part) {
-    k_field_energy<<<fdtd_blocks(g), FDTD_NT, 0, st>>>(EB, g, wf_part);
+    k_field_energy<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, g, wf_part);
     return cudaGetLastError();
 }
 

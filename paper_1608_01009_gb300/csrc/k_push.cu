@@ -22,6 +22,8 @@
 //   R = double: every value in FP64.  R = float (mixed): offsets, momenta,
 //   field tile (from the FP32 field copy), interpolation and the shared J tile
 //   in FP32; the merge into J and the kinetic-energy sum in FP64.
+#include <type_traits>
+
 #include "pic_internal.cuh"
 
 namespace picgb {
@@ -29,19 +31,75 @@ namespace picgb {
 
 
 template <class R>
+__device__ __forceinline__ R prm(double d, float f);
+template <>
+__device__ __forceinline__ double prm<double>(double d, float) {
+    return d;
+}
+template <>
+__device__ __forceinline__ float prm<float>(double, float f) {
+    return f;
+}
+
+template <class R>
 __device__ __forceinline__ R lerp(R a, R b, R t) {
     return fma(t, b - a, a);
 }
 
-// Trilinear interpolation from a T^3 tile at lattice base (i,j,k), fractions (a,b,c).
+// Shared-memory field tile.  TMA lands the raw (S+4)^3 x 6 box.  For the FP64
+// kernel with S <= 4 it is then re-laid as pairs (F[i], F[i+1]) so that each
+// x-lerp reads one 16-byte vector (4 loads per component instead of 8).  The
+// FP32 kernel keeps the raw tile: its quad layout (4 loads -> 2) cost more in
+// occupancy (3 instead of 4 CTAs per SM) and bank conflicts than it saved.
+template <class R, int S>
+struct Tile {
+    static constexpr int T = S + 4, T3 = T * T * T;
+    static constexpr bool kExpand = sizeof(R) == 8 && S <= 4;
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+};
+
 template <class R, int T>
-__device__ __forceinline__ R tri(const R* __restrict__ F, int i, int j, int k, R a, R b, R c) {
+__device__ __forceinline__ R tri_raw(const R* __restrict__ F, int i, int j, int k, R a, R b, R c) {
     const R* q = F + (k * T + j) * T + i;
     R c00 = lerp(q[0], q[1], a);
     R c10 = lerp(q[T], q[T + 1], a);
     R c01 = lerp(q[T * T], q[T * T + 1], a);
     R c11 = lerp(q[T * T + T], q[T * T + T + 1], a);
     return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
+}
+
+template <int T>
+__device__ __forceinline__ float tri_x(const float4* __restrict__ Q, int i, int j, int k, float a, float b, float c) {
+    const float4 p = Q[(k * T + j) * T + i], q = Q[((k + 1) * T + j) * T + i];
+    const float c00 = lerp(p.x, p.y, a), c10 = lerp(p.z, p.w, a);
+    const float c01 = lerp(q.x, q.y, a), c11 = lerp(q.z, q.w, a);
+    return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
+}
+
+template <int T>
+__device__ __forceinline__ double tri_x(const double2* __restrict__ D, int i, int j, int k, double a, double b,
+                                        double c) {
+    const int o = (k * T + j) * T + i;
+    const double2 p0 = D[o], p1 = D[o + T], q0 = D[o + T * T], q1 = D[o + T * T + T];
+    const double c00 = lerp(p0.x, p0.y, a), c10 = lerp(p1.x, p1.y, a);
+    const double c01 = lerp(q0.x, q0.y, a), c11 = lerp(q1.x, q1.y, a);
+    return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
+}
+
+// Build the vector tile X from the raw tile F (entries never read by tri_x --
+// the last x (and, for quads, y) plane -- are skipped).
+template <int T, int NT>
+__device__ __forceinline__ void expand_tile(const float* __restrict__ F, float4* __restrict__ X) {
+    for (int e = threadIdx.x; e < 6 * T * T * T; e += NT) {
+        const int i = e % T, j = (e / T) % T;
+        if (i < T - 1 && j < T - 1) X[e] = make_float4(F[e], F[e + 1], F[e + T], F[e + T + 1]);
+    }
+}
+template <int T, int NT>
+__device__ __forceinline__ void expand_tile(const double* __restrict__ F, double2* __restrict__ X) {
+    for (int e = threadIdx.x; e < 6 * T * T * T; e += NT) {
+        if (e % T < T - 1) X[e] = make_double2(F[e], F[e + 1]);
+    }
 }
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -159,7 +217,7 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
 // One particle per lane; all 32 lanes of the warp call it (lanes without a
 // particle pass valid = false).  Returns w (gamma - 1) of the new state.
 template <class R, int S>
-__device__ __forceinline__ R push_lane(const R* __restrict__ F, R* Jt, const PStore<R>& ps, int p, bool valid,
+__device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const PStore<R>& ps, int p, bool valid,
                                        const PushParams& pp, int c0x, int c0y, int c0z, int* err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
     const GridDev& g = pp.g;
@@ -194,15 +252,28 @@ __device__ __forceinline__ R push_lane(const R* __restrict__ F, R* Jt, const PSt
     const bool sxb = lt_half(fx), syb = lt_half(fy), szb = lt_half(fz);
     const int hx = sxb ? tx - 1 : tx, hy = syb ? ty - 1 : ty, hz = szb ? tz - 1 : tz;
     const R gxf = fx + (sxb ? hf : -hf), gyf = fy + (syb ? hf : -hf), gzf = fz + (szb ? hf : -hf);
-    const R Ex = tri<R, T>(F + 0 * T3, hx, ty, tz, gxf, fy, fz);
-    const R Ey = tri<R, T>(F + 1 * T3, tx, hy, tz, fx, gyf, fz);
-    const R Ez = tri<R, T>(F + 2 * T3, tx, ty, hz, fx, fy, gzf);
-    const R Bx = tri<R, T>(F + 3 * T3, tx, hy, hz, fx, gyf, gzf);
-    const R By = tri<R, T>(F + 4 * T3, hx, ty, hz, gxf, fy, gzf);
-    const R Bz = tri<R, T>(F + 5 * T3, hx, hy, tz, gxf, gyf, fz);
+    R Ex, Ey, Ez, Bx, By, Bz;
+    if constexpr (Tile<R, S>::kExpand) {
+        using V = typename Tile<R, S>::V;
+        const V* X = static_cast<const V*>(Fv);
+        Ex = tri_x<T>(X + 0 * T3, hx, ty, tz, gxf, fy, fz);
+        Ey = tri_x<T>(X + 1 * T3, tx, hy, tz, fx, gyf, fz);
+        Ez = tri_x<T>(X + 2 * T3, tx, ty, hz, fx, fy, gzf);
+        Bx = tri_x<T>(X + 3 * T3, tx, hy, hz, fx, gyf, gzf);
+        By = tri_x<T>(X + 4 * T3, hx, ty, hz, gxf, fy, gzf);
+        Bz = tri_x<T>(X + 5 * T3, hx, hy, tz, gxf, gyf, fz);
+    } else {
+        const R* F = static_cast<const R*>(Fv);
+        Ex = tri_raw<R, T>(F + 0 * T3, hx, ty, tz, gxf, fy, fz);
+        Ey = tri_raw<R, T>(F + 1 * T3, tx, hy, tz, fx, gyf, fz);
+        Ez = tri_raw<R, T>(F + 2 * T3, tx, ty, hz, fx, fy, gzf);
+        Bx = tri_raw<R, T>(F + 3 * T3, tx, hy, hz, fx, gyf, gzf);
+        By = tri_raw<R, T>(F + 4 * T3, hx, ty, hz, gxf, fy, gzf);
+        Bz = tri_raw<R, T>(F + 5 * T3, hx, hy, tz, gxf, gyf, fz);
+    }
 
     // ---- Boris: half electric kick, rotation, half electric kick
-    const R h = R(pp.qdt2m);
+    const R h = prm<R>(pp.qdt2m, pp.qdt2m_f);
     const R umx = fma(h, Ex, ux), umy = fma(h, Ey, uy), umz = fma(h, Ez, uz);
     const R hg = h * rsqrt(fma(umx, umx, fma(umy, umy, fma(umz, umz, R(1)))));
     const R tbx = hg * Bx, tby = hg * By, tbz = hg * Bz;
@@ -218,7 +289,8 @@ __device__ __forceinline__ R push_lane(const R* __restrict__ F, R* Jt, const PSt
     // ---- move: displacement in cells, x^{n+1} = x^n + dt u / gamma
     const R u2p1 = fma(ux, ux, fma(uy, uy, fma(uz, uz, R(1))));
     const R gi = rsqrt(u2p1);
-    const R dx = ux * (gi * R(pp.dtd[0])), dy = uy * (gi * R(pp.dtd[1])), dz = uz * (gi * R(pp.dtd[2]));
+    const R dx = ux * (gi * prm<R>(pp.dtd[0], pp.dtd_f[0])), dy = uy * (gi * prm<R>(pp.dtd[1], pp.dtd_f[1])),
+            dz = uz * (gi * prm<R>(pp.dtd[2], pp.dtd_f[2]));
     const R bx = fx + dx, by = fy + dy, bz = fz + dz;  // end point in the start cell's frame
     const int sx = cell_shift(bx), sy = cell_shift(by), sz = cell_shift(bz);
     if (act && ((unsigned)(lx + sx + 1) > (unsigned)(S + 1) || (unsigned)(ly + sy + 1) > (unsigned)(S + 1) ||
@@ -232,7 +304,8 @@ __device__ __forceinline__ R push_lane(const R* __restrict__ F, R* Jt, const PSt
     // ---- Villasenor-Buneman deposit into the shared J tile (tile origin = cell c0-1)
     const bool dep = act && w != R(0);
     const R wq = dep ? w : R(0);
-    const R Qx = R(pp.cq[0]) * wq, Qy = R(pp.cq[1]) * wq, Qz = R(pp.cq[2]) * wq;
+    const R Qx = prm<R>(pp.cq[0], pp.cq_f[0]) * wq, Qy = prm<R>(pp.cq[1], pp.cq_f[1]) * wq,
+            Qz = prm<R>(pp.cq[2], pp.cq_f[2]) * wq;
     const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
     const int nseg = 1 + (sx != 0) + (sy != 0) + (sz != 0);
     if (!__any_sync(FULL, dep && nseg > 1)) {
@@ -288,15 +361,27 @@ __device__ __forceinline__ R push_lane(const R* __restrict__ F, R* Jt, const PSt
     return gone ? R(0) : w * fma(u2p1, gi, R(-1));
 }
 
+// Resident CTAs per SM the register budget is cut for (FP32: 4 CTAs of 256
+// threads at 64 registers; the FP64 kernel needs ~100 registers, i.e. 2).
+template <class R>
+constexpr int push_min_blocks() {
+    return sizeof(R) == 4 ? 4 : 2;
+}
+
 template <class R, int S, int NT>
-__global__ void __launch_bounds__(NT) k_push(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<R> ps,
+__global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<R> ps,
                                             const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
                                             double* __restrict__ J, double* __restrict__ ek_part,
                                             int* __restrict__ err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
+    constexpr bool kExpand = Tile<R, S>::kExpand;
+    using V = typename Tile<R, S>::V;
     extern __shared__ unsigned char smem_raw[];
+    // smem: raw TMA tile (re-used as the J tile once expanded) | vector tile
     R* F = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    R* Jt = F + 6 * T3;
+    R* Jt = kExpand ? F : F + 6 * T3;
+    V* X = reinterpret_cast<V*>(F + 6 * T3);
+    const void* Fuse = kExpand ? static_cast<const void*>(X) : static_cast<const void*>(F);
     __shared__ uint64_t bar;
     __shared__ double red[NT / 32];
     const GridDev& g = pp.g;
@@ -319,18 +404,25 @@ __global__ void __launch_bounds__(NT) k_push(const __grid_constant__ CUtensorMap
             // field tile: cells c0-2 .. c0+S+1, i.e. padded index c0 .. c0+S+3
             tma_load_4d(F, &tmEB, c0x, c0y, c0z, 0, &bar);
         }
-        for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);
+        if (!kExpand)
+            for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);
         const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
             return;
         }
         phase ^= 1u;
+        if (kExpand) {
+            expand_tile<T, NT>(F, X);
+            __syncthreads();
+            for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);  // J tile over the raw tile
+            __syncthreads();
+        }
         const int end = ch.start + ch.count;
         R ek_chunk = R(0);  // at most CHUNK / NT particles per lane
         for (int base = ch.start + warp * 32; base < end; base += NT) {
             const int p = base + lane;
-            ek_chunk += push_lane<R, S>(F, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err);
+            ek_chunk += push_lane<R, S>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err);
         }
         ek += (double)ek_chunk;
         __syncthreads();
@@ -357,6 +449,8 @@ constexpr int PUSH_NT = 256;
 template <class R, int S>
 size_t push_smem_bytes() {
     constexpr int T = S + 4, TJ = S + 3;
+    if (Tile<R, S>::kExpand)
+        return 128 + sizeof(R) * 6 * T * T * T + sizeof(typename Tile<R, S>::V) * 6 * T * T * T;
     return 128 + sizeof(R) * (6 * T * T * T + 3 * TJ * TJ * TJ);
 }
 

@@ -31,10 +31,10 @@ constexpr int SCAN_PER = 4;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_PER;  // keys per tile; a multiple of every S^3
 
 __device__ __forceinline__ int cell_key(const GridDev& g, int cp) {
-    const int S = g.S;
+    const int sh = g.Sshift, m = g.S - 1;
     const int ix = cell_x(cp), iy = cell_y(cp), iz = cell_z(cp);
-    const int sc = ix / S + g.nsc[0] * (iy / S + g.nsc[1] * (iz / S));
-    return (sc * S + iz % S) * S * S + (iy % S) * S + ix % S;
+    const int sc = (ix >> sh) + g.nsc[0] * ((iy >> sh) + g.nsc[1] * (iz >> sh));
+    return (((sc << sh) + (iz & m)) << (2 * sh)) + ((iy & m) << sh) + (ix & m);
 }
 
 template <class R>

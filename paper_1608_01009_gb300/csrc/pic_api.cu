@@ -207,6 +207,11 @@ PushParams make_params(const pic_ctx* c, const Species& s) {
         pp.cq[a] = s.q / (c->g.dt * c->g.d[(a + 1) % 3] * c->g.d[(a + 2) % 3]);
     }
     pp.mass = s.m;
+    pp.qdt2m_f = (float)pp.qdt2m;
+    for (int a = 0; a < 3; ++a) {
+        pp.dtd_f[a] = (float)pp.dtd[a];
+        pp.cq_f[a] = (float)pp.cq[a];
+    }
     return pp;
 }
 
@@ -542,6 +547,7 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
         g.n[a] = gd->n[a];
         g.np[a] = gd->n[a] + 2 * PAD;
         g.d[a] = gd->d[a];
+        g.rd[a] = 1.0 / gd->d[a];
         g.bc[a] = gd->bc[a];
         g.nsc[a] = gd->n[a] / gd->supercell;
         dmax = std::fmax(dmax, gd->dt / gd->d[a]);
@@ -549,9 +555,11 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
     g.P = (long long)g.np[0] * g.np[1] * g.np[2];
     g.dt = gd->dt;
     g.S = gd->supercell;
+    g.Sshift = g.S == 2 ? 1 : (g.S == 4 ? 2 : 3);
     g.nbins = g.nsc[0] * g.nsc[1] * g.nsc[2];
     g.absorb_cells = gd->absorb_cells;
     g.absorb_sigma = gd->absorb_sigma;
+    g.absorb_rL = gd->absorb_cells > 0 ? 1.0 / gd->absorb_cells : 0.0;
     c->K = gd->sort_interval > 0 ? gd->sort_interval : (int)std::floor((1.0 - 1e-9) / dmax);
     if (c->K < 1) c->K = 1;
     auto bail = [&](int code) {

@@ -35,13 +35,16 @@ struct GridDev {
     int np[3];     // padded extent n + 2 PAD
     long long P;   // padded volume
     double d[3];
+    double rd[3];  // 1 / d
     double dt;
     int bc[3];
     int S;         // supercell edge in cells
+    int Sshift;    // log2(S)
     int nsc[3];    // supercells per axis
     int nbins;
     int absorb_cells;
     double absorb_sigma;
+    double absorb_rL;  // 1 / absorb_cells (0 without a layer)
 };
 
 template <class R>
@@ -66,6 +69,9 @@ struct PushParams {
     double dtd[3];  // dt / d[a]: velocity (in c) -> displacement in cells
     double cq[3];   // q / (dt d[p] d[r]): current density per unit weight and cell displacement
     double mass;
+    // FP32 copies for the mixed kernel (a double -> float conversion runs on
+    // the FP64 pipe, so none is left inside the particle loop)
+    float qdt2m_f, dtd_f[3], cq_f[3];
 };
 
 constexpr int CHUNK = 4096;  // most particles of one supercell handled by one CTA pass
@@ -152,16 +158,18 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Fixed-order block sum (deterministic for a fixed block size); result valid in thread 0.
+// Fixed-order block sum (deterministic for a fixed block shape); result valid
+// in the block's first thread.  Blocks may be 1-, 2- or 3-D (NT threads).
 template <int NT>
 __device__ double block_sum(double v, double* scratch) {
     v = warp_sum(v);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int w = tid >> 5, l = tid & 31;
     __syncthreads();
     if (l == 0) scratch[w] = v;
     __syncthreads();
     double s = 0.0;
-    if (threadIdx.x == 0)
+    if (tid == 0)
         for (int i = 0; i < NT / 32; ++i) s += scratch[i];
     return s;
 }
