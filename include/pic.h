@@ -201,6 +201,33 @@ PIC_API int pic_stage_times(pic_ctx* ctx, double out[4]);
 /* Kernels this context has launched since creation (or the last reset). */
 PIC_API int pic_launch_count(pic_ctx* ctx, int64_t* n, int reset);
 
+/* Differentiable runs: a hand-written discrete adjoint of the whole step
+ * (push, deposit and FDTD) with checkpointed recomputation.
+ *
+ * pic_tape_forward advances nsteps whole steps from the current state on the
+ * differentiable FP64 path -- the same step as pic_step (cloud-in-cell
+ * gather, Boris push, Villasenor-Buneman deposit, Yee FDTD; Sec. 2-3), with
+ * the particles kept in id order and no supercell sort, so that any segment
+ * can be replayed exactly -- saving the FP64 state every `ckpt_every` steps in
+ * library-owned device memory.  *wk receives the final kinetic energy
+ * W_K = sum m w (gamma - 1).  The context continues from the final state.
+ *
+ * pic_tape_backward then computes the gradient of
+ *     L = wk_weight * W_K(final) + <gE, E(final)> + <gB, B(final)>
+ * with respect to the fields at the start of the tape: for each checkpoint
+ * segment in reverse it restores the checkpoint, recomputes the segment while
+ * keeping every step's state, and runs the adjoint kernels backwards through
+ * it.  gE, gB: unpadded device arrays or NULL (zero); dE0, dB0: unpadded
+ * device arrays that receive dL/dE(start), dL/dB(start), or NULL.  Both calls
+ * synchronise.  pic_tape_particle_grad then copies dL/d(x, y, z, ux, uy, uz)
+ * of the starting particles of a species, in id order (device arrays of the
+ * species' id count, NULL entries skipped; positions in physical units).
+ * PIC_ERR_STATE if no tape has been recorded. */
+PIC_API int pic_tape_forward(pic_ctx* ctx, int nsteps, int ckpt_every, double* wk);
+PIC_API int pic_tape_backward(pic_ctx* ctx, double wk_weight, const double* const gE[3], const double* const gB[3],
+                              double* const dE0[3], double* const dB0[3]);
+PIC_API int pic_tape_particle_grad(pic_ctx* ctx, int species, double* const dP[6]);
+
 /* Field energy W_F = 1/2 dx dy dz sum (E^2 + B^2) of caller-provided fields,
  * allocating nothing.  The paper has no counterpart: this is a library
  * facility for callers that cannot allocate device memory -- a host framework

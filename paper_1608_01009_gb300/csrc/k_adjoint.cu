@@ -1,0 +1,674 @@
+// Differentiable FP64 path: the PIC step on id-ordered particles, and its
+// hand-written discrete adjoint.
+//
+// Forward (one thread per particle; the same step as the fused kernel --
+// cloud-in-cell gather, relativistic Boris push, move and Villasenor-Buneman
+// deposit, arXiv:1608.01009 Secs. 2-3 -- but with particles kept in a fixed
+// order, gathering from the ghost-padded FP64 field buffer in global memory
+// and depositing with global atomics).  No sort is needed, so a run can be
+// replayed from a checkpoint particle for particle.
+//
+// Adjoint of one step, given the cotangents of the new state (lambda_x of
+// x^{n+1}, lambda_u of u^{n+1/2}, lambda_E of E^{n+1}, lambda_B of B^{n+1}):
+//   fields    the Yee sub-steps in reverse.  With C_E the forward-difference
+//             curl (E lattice -> B lattice) and C_B the backward-difference
+//             curl (B -> E), C_B = C_E^T (also with zero fields outside an
+//             absorbing axis), and the damping masks M are diagonal:
+//               B^{n+1} = M_B (B' - h C_E E^{n+1})     -> lB' = M_B lB1, lE1 -= h C_B lB'
+//               E^{n+1} = M_E (E^n + dt C_B B' - dt J)  -> lE^n = M_E lE1, lB' += dt C_E lE^n,
+//                                                          lJ = -dt lE^n
+//               B'      = M_B (B^n - h C_E E^n)        -> lB^n = M_B lB', lE^n -= h C_B lB^n
+//   particles reverse mode through deposit (the edge currents as functions of
+//             the piece start, displacement and crossing times), move, Boris
+//             and the trilinear gather (a weighted scatter of lambda_E,
+//             lambda_B to the grid and a position gradient).
+#include "pic_internal.cuh"
+
+namespace picgb {
+
+constexpr int TAPE_NT = 256;
+
+__device__ __forceinline__ double stag(int comp, int axis, bool magnetic) {
+    return magnetic ? (comp == axis ? 0.0 : 0.5) : (comp == axis ? 0.5 : 0.0);
+}
+
+// Lattice base and fractions of component c (0..5: Ex..Ez, Bx..Bz) at xi.
+__device__ __forceinline__ void lattice(int c, const double xi[3], int base[3], double f[3]) {
+    for (int a = 0; a < 3; ++a) {
+        const double s = xi[a] - stag(c % 3, a, c >= 3);
+        const double fl = floor(s);
+        base[a] = (int)fl;
+        f[a] = s - fl;
+    }
+}
+
+__device__ __forceinline__ double tri_val(const double v[8], const double f[3]) {
+    const double c00 = fma(f[0], v[1] - v[0], v[0]), c10 = fma(f[0], v[3] - v[2], v[2]);
+    const double c01 = fma(f[0], v[5] - v[4], v[4]), c11 = fma(f[0], v[7] - v[6], v[6]);
+    const double c0 = fma(f[1], c10 - c00, c00), c1 = fma(f[1], c11 - c01, c01);
+    return fma(f[2], c1 - c0, c0);
+}
+
+// 8 corner values v[bx + 2 by + 4 bz] of component c around `base`.
+__device__ __forceinline__ void corners(const double* EB, const GridDev& g, int c, const int base[3], double v[8]) {
+    const double* F = EB + (long long)c * g.P;
+    for (int q = 0; q < 8; ++q) v[q] = F[pidx(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1), base[2] + (q >> 2))];
+}
+
+__device__ __forceinline__ void boris(double u[3], const double E[3], const double B[3], double h) {
+    double um[3], t[3], s[3], up[3];
+    for (int a = 0; a < 3; ++a) um[a] = fma(h, E[a], u[a]);
+    const double hg = h * rsqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], 1.0))));
+    for (int a = 0; a < 3; ++a) t[a] = hg * B[a];
+    const double k = 2.0 / (1.0 + fma(t[0], t[0], fma(t[1], t[1], t[2] * t[2])));
+    for (int a = 0; a < 3; ++a) s[a] = k * t[a];
+    up[0] = fma(um[1], t[2], fma(-um[2], t[1], um[0]));
+    up[1] = fma(um[2], t[0], fma(-um[0], t[2], um[1]));
+    up[2] = fma(um[0], t[1], fma(-um[1], t[0], um[2]));
+    u[0] = fma(h, E[0], fma(up[1], s[2], fma(-up[2], s[1], um[0])));
+    u[1] = fma(h, E[1], fma(up[2], s[0], fma(-up[0], s[2], um[1])));
+    u[2] = fma(h, E[2], fma(up[0], s[1], fma(-up[1], s[0], um[2])));
+}
+
+__device__ __forceinline__ void cross(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Reverse mode of the Boris step: given lun (cotangent of the new u), returns
+// lu (old u) and adds the cotangents of the particle fields into lE, lB.
+__device__ void boris_adjoint(const double u[3], const double E[3], const double B[3], double h, const double lun[3],
+                              double lu[3], double lE[3], double lB[3]) {
+    double um[3], t[3], s[3], up[3];
+    for (int a = 0; a < 3; ++a) um[a] = fma(h, E[a], u[a]);
+    const double gm = sqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], 1.0))));
+    const double gg = h / gm;
+    for (int a = 0; a < 3; ++a) t[a] = gg * B[a];
+    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double k = 2.0 / (1.0 + t2);
+    for (int a = 0; a < 3; ++a) s[a] = k * t[a];
+    double umxt[3];
+    cross(um, t, umxt);
+    for (int a = 0; a < 3; ++a) up[a] = um[a] + umxt[a];
+    // un = upl + h E ; upl = um + up x s
+    double lum[3], lup[3], ls[3], lt[3], tmp[3];
+    for (int a = 0; a < 3; ++a) {
+        lE[a] += h * lun[a];
+        lum[a] = lun[a];
+    }
+    cross(s, lun, lup);  // lambda_up = s x lambda_upl
+    cross(lun, up, ls);  // lambda_s = lambda_upl x up
+    // up = um + um x t
+    cross(t, lup, tmp);
+    for (int a = 0; a < 3; ++a) lum[a] += lup[a] + tmp[a];
+    cross(lup, um, lt);  // lambda_t = lambda_up x um
+    // s = k t, k = 2 / (1 + t.t)
+    const double lk = ls[0] * t[0] + ls[1] * t[1] + ls[2] * t[2];
+    const double lt2 = -0.5 * k * k * lk;
+    for (int a = 0; a < 3; ++a) lt[a] += k * ls[a] + 2.0 * t[a] * lt2;
+    // t = g B, g = h / gm, gm = sqrt(1 + um.um)
+    const double lg = lt[0] * B[0] + lt[1] * B[1] + lt[2] * B[2];
+    for (int a = 0; a < 3; ++a) lB[a] += gg * lt[a];
+    const double lgm = -lg * gg / gm;
+    for (int a = 0; a < 3; ++a) lum[a] += lgm * um[a] / gm;
+    // um = u + h E
+    for (int a = 0; a < 3; ++a) {
+        lu[a] = lum[a];
+        lE[a] += h * lum[a];
+    }
+}
+
+// The pieces of the move a -> a + d (a relative to cell cell0, in cells): the
+// crossing parameters t (1 where an axis is not crossed), sorted with the axis
+// each belongs to.
+struct Pieces {
+    double t[3];
+    int ax[3];
+    bool cr[3];  // the axis is crossed
+    int n;       // number of pieces
+};
+
+__device__ __forceinline__ Pieces pieces_of(const double a[3], const double d[3]) {
+    Pieces P;
+    P.n = 1;
+    for (int c = 0; c < 3; ++c) {
+        const double b = a[c] + d[c];
+        P.ax[c] = c;
+        P.cr[c] = b >= 1.0 || b < 0.0;
+        if (P.cr[c]) {
+            P.t[c] = ((b >= 1.0 ? 1.0 : 0.0) - a[c]) / d[c];
+            P.n += 1;
+        } else {
+            P.t[c] = 1.0;
+        }
+    }
+    // sort (t, axis) ascending; on a tie a crossed axis goes first, so the
+    // first n - 1 entries are exactly the crossings
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2 - i; ++j)
+            if (P.t[j + 1] < P.t[j] || (P.t[j + 1] == P.t[j] && P.cr[j + 1] && !P.cr[j])) {
+                const double tt = P.t[j];
+                P.t[j] = P.t[j + 1];
+                P.t[j + 1] = tt;
+                const int aa = P.ax[j];
+                P.ax[j] = P.ax[j + 1];
+                P.ax[j + 1] = aa;
+                const bool cc = P.cr[j];
+                P.cr[j] = P.cr[j + 1];
+                P.cr[j + 1] = cc;
+            }
+    return P;
+}
+
+__device__ __forceinline__ int off_of(double m) { return m < 0.0 ? -1 : (m >= 1.0 ? 1 : 0); }
+
+// Forward deposit of the move from cell0 + a with displacement d into J
+// (padded, global atomics).
+__device__ void deposit_global(double* J, const GridDev& g, const int cell0[3], const double a[3], const double d[3],
+                               const double Q[3]) {
+    const Pieces P = pieces_of(a, d);
+    double ta = 0.0;
+    for (int s = 0; s < P.n; ++s) {
+        const double tb = s + 1 < P.n ? P.t[s] : 1.0;
+        if (tb > ta) {
+            double pa[3], dd[3];
+            int cell[3];
+            for (int c = 0; c < 3; ++c) {
+                pa[c] = fma(ta, d[c], a[c]);
+                dd[c] = (tb - ta) * d[c];
+                const int o = off_of(fma(0.5, dd[c], pa[c]));
+                cell[c] = cell0[c] + o;
+                pa[c] -= o;
+            }
+            double m[3], om[3];
+            for (int c = 0; c < 3; ++c) {
+                m[c] = fma(0.5, dd[c], pa[c]);
+                om[c] = 1.0 - m[c];
+            }
+            for (int c = 0; c < 3; ++c) {
+                const int p = (c + 1) % 3, r = (c + 2) % 3;
+                const double q = Q[c] * dd[c], k = dd[p] * dd[r] * (1.0 / 12.0);
+                double* Jc = J + (long long)c * g.P;
+                for (int s1 = 0; s1 < 2; ++s1)
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const double wp = s1 ? m[p] : om[p], wr = s2 ? m[r] : om[r];
+                        const double sig = s1 == s2 ? 1.0 : -1.0;
+                        int idx[3] = {cell[0], cell[1], cell[2]};
+                        idx[p] += s1;
+                        idx[r] += s2;
+                        atomicAdd(&Jc[pidx(g, idx[0], idx[1], idx[2])], q * fma(sig, k, wp * wr));
+                    }
+            }
+        }
+        ta = tb;
+    }
+}
+
+// Reverse mode of deposit_global: reads lJ (padded, ghosts filled) and adds
+// the cotangents of the start a and displacement d.
+__device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int cell0[3], const double a[3],
+                                const double d[3], const double Q[3], double la[3], double ld[3]) {
+    const Pieces P = pieces_of(a, d);
+    double lt[3] = {0.0, 0.0, 0.0};  // cotangents of the sorted crossing parameters
+    double ta = 0.0;
+    for (int s = 0; s < P.n; ++s) {
+        const double tb = s + 1 < P.n ? P.t[s] : 1.0;
+        if (tb > ta) {
+            double pa[3], dd[3];
+            int cell[3];
+            for (int c = 0; c < 3; ++c) {
+                pa[c] = fma(ta, d[c], a[c]);
+                dd[c] = (tb - ta) * d[c];
+                const int o = off_of(fma(0.5, dd[c], pa[c]));
+                cell[c] = cell0[c] + o;
+                pa[c] -= o;
+            }
+            double m[3], om[3];
+            for (int c = 0; c < 3; ++c) {
+                m[c] = fma(0.5, dd[c], pa[c]);
+                om[c] = 1.0 - m[c];
+            }
+            double lpa[3] = {0, 0, 0}, ldd[3] = {0, 0, 0};
+            for (int c = 0; c < 3; ++c) {
+                const int p = (c + 1) % 3, r = (c + 2) % 3;
+                const double* Lc = LJ + (long long)c * g.P;
+                int i0[3] = {cell[0], cell[1], cell[2]};
+                double L[2][2];
+                for (int s1 = 0; s1 < 2; ++s1)
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        int idx[3] = {i0[0], i0[1], i0[2]};
+                        idx[p] += s1;
+                        idx[r] += s2;
+                        L[s1][s2] = Lc[pidx(g, idx[0], idx[1], idx[2])];
+                    }
+                // f = Q d_c [Sum L W_p W_r + K d_p d_r / 12]
+                const double S = L[0][0] * om[p] * om[r] + L[1][0] * m[p] * om[r] + L[0][1] * om[p] * m[r] +
+                                 L[1][1] * m[p] * m[r];
+                const double K = L[0][0] - L[1][0] - L[0][1] + L[1][1];
+                const double Dp = -L[0][0] * om[r] + L[1][0] * om[r] - L[0][1] * m[r] + L[1][1] * m[r];
+                const double Dr = -L[0][0] * om[p] - L[1][0] * m[p] + L[0][1] * om[p] + L[1][1] * m[p];
+                const double qd = Q[c] * dd[c];
+                ldd[c] += Q[c] * (S + K * dd[p] * dd[r] * (1.0 / 12.0));
+                lpa[p] += qd * Dp;
+                lpa[r] += qd * Dr;
+                ldd[p] += 0.5 * qd * Dp + qd * K * dd[r] * (1.0 / 12.0);
+                ldd[r] += 0.5 * qd * Dr + qd * K * dd[p] * (1.0 / 12.0);
+            }
+            // pa = a + ta d - o, dd = (tb - ta) d
+            double lta = 0.0, ltb = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                la[c] += lpa[c];
+                ld[c] += ta * lpa[c] + (tb - ta) * ldd[c];
+                lta += d[c] * (lpa[c] - ldd[c]);
+                ltb += d[c] * ldd[c];
+            }
+            if (s > 0) lt[s - 1] += lta;
+            if (s + 1 < P.n) lt[s] += ltb;
+        }
+        ta = tb;
+    }
+    // t = (face - a_ax) / d_ax
+    for (int s = 0; s + 1 < P.n; ++s) {
+        const int c = P.ax[s];
+        la[c] -= lt[s] / d[c];
+        ld[c] -= lt[s] * P.t[s] / d[c];
+    }
+}
+
+// One forward step of every particle.
+__global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, StepParams sp, const double* __restrict__ EB,
+                                                      double* __restrict__ J) {
+    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
+    if (p >= n || !T.act[p]) return;
+    const GridDev& g = sp.g;
+    double xi[3] = {T.xi[0][p], T.xi[1][p], T.xi[2][p]};
+    double u[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
+    double F[6];
+    for (int c = 0; c < 6; ++c) {
+        int base[3];
+        double f[3], v[8];
+        lattice(c, xi, base, f);
+        corners(EB, g, c, base, v);
+        F[c] = tri_val(v, f);
+    }
+    boris(u, F, F + 3, sp.qdt2m);
+    const double gi = rsqrt(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
+    double d[3], a[3];
+    int cell0[3];
+    for (int c = 0; c < 3; ++c) {
+        d[c] = u[c] * (gi * sp.dtd[c]);
+        const double fl = floor(xi[c]);
+        cell0[c] = (int)fl;
+        a[c] = xi[c] - fl;
+    }
+    const double w = T.w[p];
+    if (w != 0.0 && sp.cq[0] != 0.0) {
+        const double Q[3] = {sp.cq[0] * w, sp.cq[1] * w, sp.cq[2] * w};
+        deposit_global(J, g, cell0, a, d, Q);
+    }
+    bool gone = false;
+    for (int c = 0; c < 3; ++c) {
+        double x1 = xi[c] + d[c];
+        if (g.bc[c] == 0) {
+            if (x1 < 0.0) x1 += g.n[c];
+            if (x1 >= g.n[c]) x1 -= g.n[c];
+        } else if (x1 < 0.0 || x1 >= g.n[c]) {
+            gone = true;
+        }
+        T.xi[c][p] = x1;
+        T.u[c][p] = u[c];
+    }
+    if (gone) T.act[p] = 0;
+}
+
+// Cotangent of the final kinetic energy: lambda_u = weight * m w u / gamma, lambda_x = 0.
+__global__ void __launch_bounds__(TAPE_NT) k_tape_seed(TapeDev T, LamDev L, long long n, double mass, double weight) {
+    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
+    if (p >= n) return;
+    const double u[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
+    const double gi = rsqrt(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
+    const double s = T.act[p] ? weight * mass * T.w[p] * gi : 0.0;
+    for (int c = 0; c < 3; ++c) {
+        L.u[c][p] = s * u[c];
+        L.xi[c][p] = 0.0;
+    }
+}
+
+// Reverse of one particle step.  T holds the state at step n (x^n, u^{n-1/2});
+// L holds the cotangents of x^{n+1}, u^{n+1/2} on entry and of x^n, u^{n-1/2}
+// on exit; EB = E^n, B^n; LJ = lambda_J (ghosts filled); scat receives the
+// gather cotangents lambda_E, lambda_B (padded, atomics; ghosts folded later).
+__global__ void __launch_bounds__(TAPE_NT) k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp,
+                                                         const double* __restrict__ EB, const double* __restrict__ LJ,
+                                                         double* __restrict__ scat) {
+    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
+    if (p >= n || !T.act[p]) return;  // inactive: the step is the identity
+    const GridDev& g = sp.g;
+    const double xi[3] = {T.xi[0][p], T.xi[1][p], T.xi[2][p]};
+    const double u0[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
+    // recompute the forward step
+    double F[6], fr[6][3], vv[6][8];
+    int bs[6][3];
+    for (int c = 0; c < 6; ++c) {
+        lattice(c, xi, bs[c], fr[c]);
+        corners(EB, g, c, bs[c], vv[c]);
+        F[c] = tri_val(vv[c], fr[c]);
+    }
+    double u1[3] = {u0[0], u0[1], u0[2]};
+    boris(u1, F, F + 3, sp.qdt2m);
+    const double u2p1 = fma(u1[0], u1[0], fma(u1[1], u1[1], fma(u1[2], u1[2], 1.0)));
+    const double gi = rsqrt(u2p1);
+    double d[3], a[3];
+    int cell0[3];
+    for (int c = 0; c < 3; ++c) {
+        d[c] = u1[c] * (gi * sp.dtd[c]);
+        const double fl = floor(xi[c]);
+        cell0[c] = (int)fl;
+        a[c] = xi[c] - fl;
+    }
+    // cotangents of the outputs
+    double lx1[3] = {L.xi[0][p], L.xi[1][p], L.xi[2][p]};
+    double lu1[3] = {L.u[0][p], L.u[1][p], L.u[2][p]};
+    // deposit
+    double la[3] = {0, 0, 0}, ld[3] = {0, 0, 0};
+    const double w = T.w[p];
+    if (w != 0.0 && sp.cq[0] != 0.0) {
+        const double Q[3] = {sp.cq[0] * w, sp.cq[1] * w, sp.cq[2] * w};
+        deposit_adjoint(LJ, g, cell0, a, d, Q, la, ld);
+    }
+    // move: x^{n+1} = x^n + d, d = dtd u / gamma
+    double lx0[3];
+    for (int c = 0; c < 3; ++c) {
+        lx0[c] = lx1[c] + la[c];
+        ld[c] += lx1[c];
+    }
+    double ldv[3], dot = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        ldv[c] = sp.dtd[c] * ld[c];
+        dot += ldv[c] * u1[c];
+    }
+    const double gi3 = gi * gi * gi;
+    for (int c = 0; c < 3; ++c) lu1[c] += ldv[c] * gi - u1[c] * dot * gi3;
+    // Boris
+    double lu0[3], lF[6] = {0, 0, 0, 0, 0, 0};
+    boris_adjoint(u0, F, F + 3, sp.qdt2m, lu1, lu0, lF, lF + 3);
+    // gather: scatter lambda_F with the CIC weights, and the position gradient
+    for (int c = 0; c < 6; ++c) {
+        const double* f = fr[c];
+        const double* v = vv[c];
+        double* S = scat + (long long)c * g.P;
+        for (int q = 0; q < 8; ++q) {
+            const int bx = q & 1, by = (q >> 1) & 1, bz = q >> 2;
+            const double wq = (bx ? f[0] : 1 - f[0]) * (by ? f[1] : 1 - f[1]) * (bz ? f[2] : 1 - f[2]);
+            atomicAdd(&S[pidx(g, bs[c][0] + bx, bs[c][1] + by, bs[c][2] + bz)], lF[c] * wq);
+        }
+        double dfx = 0.0, dfy = 0.0, dfz = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            const int bx = q & 1, by = (q >> 1) & 1, bz = q >> 2;
+            const double wx = bx ? f[0] : 1 - f[0], wy = by ? f[1] : 1 - f[1], wz = bz ? f[2] : 1 - f[2];
+            dfx += (bx ? 1.0 : -1.0) * wy * wz * v[q];
+            dfy += (by ? 1.0 : -1.0) * wx * wz * v[q];
+            dfz += (bz ? 1.0 : -1.0) * wx * wy * v[q];
+        }
+        lx0[0] += lF[c] * dfx;
+        lx0[1] += lF[c] * dfy;
+        lx0[2] += lF[c] * dfz;
+    }
+    for (int c = 0; c < 3; ++c) {
+        L.xi[c][p] = lx0[c];
+        L.u[c][p] = lu0[c];
+    }
+}
+
+// Kinetic-energy partials of the tape state.
+__global__ void __launch_bounds__(TAPE_NT) k_tape_kinetic(TapeDev T, long long n, double mass, double* __restrict__ part) {
+    __shared__ double red[TAPE_NT / 32];
+    double s = 0.0;
+    for (long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x; p < n; p += (long long)gridDim.x * TAPE_NT) {
+        if (!T.act[p]) continue;
+        const double u2p1 = fma(T.u[0][p], T.u[0][p], fma(T.u[1][p], T.u[1][p], fma(T.u[2][p], T.u[2][p], 1.0)));
+        s += T.w[p] * fma(u2p1, rsqrt(u2p1), -1.0);
+    }
+    const double t = block_sum<TAPE_NT>(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t * mass;
+}
+
+// Store (binned) -> id-ordered tape arrays (positions in cells).
+template <class R>
+__global__ void __launch_bounds__(TAPE_NT) k_tape_from_store(PStore<R> ps, const long long* __restrict__ n_cur, TapeDev T,
+                                                            double* __restrict__ w_out, long long nid) {
+    const long long N = *n_cur;
+    for (long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x; p < N; p += (long long)gridDim.x * TAPE_NT) {
+        const int cp = ps.cell[p];
+        if (cp < 0) continue;
+        const long long id = ps.id[p];
+        if (id < 0 || id >= nid) continue;
+        T.xi[0][id] = (double)cell_x(cp) + (double)ps.off[0][p];
+        T.xi[1][id] = (double)cell_y(cp) + (double)ps.off[1][p];
+        T.xi[2][id] = (double)cell_z(cp) + (double)ps.off[2][p];
+        for (int c = 0; c < 3; ++c) T.u[c][id] = (double)ps.u[c][p];
+        w_out[id] = (double)ps.w[p];
+        T.act[id] = 1;
+    }
+}
+
+// Tape -> FP64 physical arrays (x,y,z,ux,uy,uz,w), for re-loading the store.
+__global__ void __launch_bounds__(TAPE_NT) k_tape_to_phys(TapeDev T, long long n, GridDev g, double* const* out) {
+    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
+    if (p >= n) return;
+    for (int c = 0; c < 3; ++c) {
+        // absent or deactivated particles are placed outside the domain so that the load drops them
+        out[c][p] = T.act[p] ? T.xi[c][p] * g.d[c] : (g.bc[c] ? -1.0 : T.xi[c][p] * g.d[c]);
+        out[3 + c][p] = T.u[c][p];
+    }
+    out[6][p] = T.w[p];
+}
+
+// Particle cotangents -> gradients in physical units (lambda_x / d).
+__global__ void __launch_bounds__(TAPE_NT) k_lam_to_phys(LamDev L, long long n, GridDev g, double* const* out) {
+    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
+    if (p >= n) return;
+    for (int c = 0; c < 3; ++c) {
+        if (out[c]) out[c][p] = L.xi[c][p] * g.rd[c];
+        if (out[3 + c]) out[3 + c][p] = L.u[c][p];
+    }
+}
+
+// ------------------------------------------------------------------ adjoint fields
+// Ghost bookkeeping as in the forward FDTD: periodic images of the owner; on
+// absorbing axes the ghosts stand for the fixed zero field outside.
+__device__ __forceinline__ void img(int i, int n, int bc, int idx[2], bool fold[2], int& cnt) {
+    idx[0] = i;
+    fold[0] = true;
+    cnt = 1;
+    if (i < PAD) {
+        idx[1] = bc == 0 ? i + n : i - PAD;
+        fold[1] = bc == 0;
+        cnt = 2;
+    } else if (i >= n - PAD) {
+        idx[1] = bc == 0 ? i - n : i + PAD;
+        fold[1] = bc == 0;
+        cnt = 2;
+    }
+}
+
+__device__ __forceinline__ double damp_of(const GridDev& g, int comp, bool magnetic, int i, int j, int k) {
+    double f = 1.0;
+    const int ijk[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a) {
+        if (g.bc[a] == 0 || g.absorb_cells <= 0) continue;
+        const double pos = ijk[a] + stag(comp, a, magnetic);
+        const double dist = fmin(pos, (double)g.n[a] - pos);
+        const double L = (double)g.absorb_cells;
+        if (dist >= L) continue;
+        const double r = (L - dist) * g.absorb_rL;
+        f *= 1.0 - g.absorb_sigma * r * r;
+    }
+    return f;
+}
+
+constexpr int AF_BX = 32, AF_BY = 8;
+
+__device__ __forceinline__ bool acell(const GridDev& g, int& i, int& j, int& k) {
+    i = blockIdx.x * AF_BX + threadIdx.x;
+    j = blockIdx.y * AF_BY + threadIdx.y;
+    k = blockIdx.z;
+    return i < g.n[0] && j < g.n[1];
+}
+
+template <class F>
+__device__ __forceinline__ void for_images(const GridDev& g, int i, int j, int k, bool only_fold, F fn) {
+    int ix[2], iy[2], iz[2], cx, cy, cz;
+    bool fx[2], fy[2], fz[2];
+    img(i, g.n[0], g.bc[0], ix, fx, cx);
+    img(j, g.n[1], g.bc[1], iy, fy, cy);
+    img(k, g.n[2], g.bc[2], iz, fz, cz);
+    for (int c = 0; c < cz; ++c)
+        for (int b = 0; b < cy; ++b)
+            for (int a = 0; a < cx; ++a) {
+                const bool f = fx[a] && fy[b] && fz[c];
+                if (only_fold && !f) continue;
+                fn(pidx(g, ix[a], iy[b], iz[c]), f, (a | b | c) == 0);
+            }
+}
+
+// L[comp] <- mask * L[comp] on the domain, copied to the periodic ghost images
+// (comp0 = 0: E components, 3: B components).
+__global__ void k_adj_mask_fill(double* __restrict__ L, GridDev g, int comp0) {
+    int i, j, k;
+    if (!acell(g, i, j, k)) return;
+    const long long o = pidx(g, i, j, k);
+    for (int c = 0; c < 3; ++c) {
+        double* A = L + (long long)(comp0 + c) * g.P;
+        const double v = A[o] * damp_of(g, c, comp0 == 3, i, j, k);
+        for_images(g, i, j, k, true, [&](long long q, bool, bool) { A[q] = v; });
+    }
+}
+
+// lE += coef * C_B lB (backward differences; reads lB ghosts).
+__global__ void k_adj_curlB(double* __restrict__ L, GridDev g, double coef) {
+    int i, j, k;
+    if (!acell(g, i, j, k)) return;
+    const long long o = pidx(g, i, j, k), sy = g.np[0], sz = (long long)g.np[0] * g.np[1];
+    const double* Bx = L + 3 * g.P;
+    const double* By = L + 4 * g.P;
+    const double* Bz = L + 5 * g.P;
+    const double rx = g.rd[0], ry = g.rd[1], rz = g.rd[2];
+    const double cx = (Bz[o] - Bz[o - sy]) * ry - (By[o] - By[o - sz]) * rz;
+    const double cy = (Bx[o] - Bx[o - sz]) * rz - (Bz[o] - Bz[o - 1]) * rx;
+    const double cz = (By[o] - By[o - 1]) * rx - (Bx[o] - Bx[o - sy]) * ry;
+    L[o] += coef * cx;
+    L[g.P + o] += coef * cy;
+    L[2 * g.P + o] += coef * cz;
+}
+
+// lB += coef * C_E lE (forward differences; reads lE ghosts); and
+// lJ = jcoef * lE on the cell and its periodic images.
+__global__ void k_adj_curlE(double* __restrict__ L, double* __restrict__ LJ, GridDev g, double coef, double jcoef) {
+    int i, j, k;
+    if (!acell(g, i, j, k)) return;
+    const long long o = pidx(g, i, j, k), sy = g.np[0], sz = (long long)g.np[0] * g.np[1];
+    const double* Ex = L;
+    const double* Ey = L + g.P;
+    const double* Ez = L + 2 * g.P;
+    const double rx = g.rd[0], ry = g.rd[1], rz = g.rd[2];
+    const double ex = Ex[o], ey = Ey[o], ez = Ez[o];
+    const double cx = (Ez[o + sy] - ez) * ry - (Ey[o + sz] - ey) * rz;
+    const double cy = (Ex[o + sz] - ex) * rz - (Ez[o + 1] - ez) * rx;
+    const double cz = (Ey[o + 1] - ey) * rx - (Ex[o + sy] - ex) * ry;
+    L[3 * g.P + o] += coef * cx;
+    L[4 * g.P + o] += coef * cy;
+    L[5 * g.P + o] += coef * cz;
+    const double e[3] = {ex, ey, ez};
+    for (int c = 0; c < 3; ++c) {
+        double* A = LJ + (long long)c * g.P;
+        const double v = jcoef * e[c];
+        for_images(g, i, j, k, true, [&](long long q, bool, bool) { A[q] = v; });
+    }
+}
+
+// L (domain cells) += scat summed over the cell and its periodic images; every
+// scat entry read is zeroed (absorbing ghosts are dropped: no field lives there).
+__global__ void k_adj_fold_add(double* __restrict__ L, double* __restrict__ scat, GridDev g) {
+    int i, j, k;
+    if (!acell(g, i, j, k)) return;
+    const long long o = pidx(g, i, j, k);
+    for (int c = 0; c < 6; ++c) {
+        double* S = scat + (long long)c * g.P;
+        double s = 0.0;
+        for_images(g, i, j, k, false, [&](long long q, bool fold, bool) {
+            if (fold) s += S[q];
+            S[q] = 0.0;
+        });
+        L[(long long)c * g.P + o] += s;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static dim3 agrid(const GridDev& g) { return dim3((g.n[0] + AF_BX - 1) / AF_BX, (g.n[1] + AF_BY - 1) / AF_BY, g.n[2]); }
+static int pgrid(long long n) { return (int)((n + TAPE_NT - 1) / TAPE_NT); }
+
+cudaError_t tape_step_launch(cudaStream_t st, const TapeDev& T, long long n, const StepParams& sp, const double* EB,
+                             double* J) {
+    if (n > 0) k_tape_step<<<pgrid(n), TAPE_NT, 0, st>>>(T, n, sp, EB, J);
+    return cudaGetLastError();
+}
+
+cudaError_t tape_seed_launch(cudaStream_t st, const TapeDev& T, const LamDev& L, long long n, double mass,
+                             double weight) {
+    if (n > 0) k_tape_seed<<<pgrid(n), TAPE_NT, 0, st>>>(T, L, n, mass, weight);
+    return cudaGetLastError();
+}
+
+cudaError_t tape_adjoint_launch(cudaStream_t st, const TapeDev& T, const LamDev& L, long long n, const StepParams& sp,
+                                const double* EB, const double* LJ, double* scat) {
+    if (n > 0) k_tape_adjoint<<<pgrid(n), TAPE_NT, 0, st>>>(T, L, n, sp, EB, LJ, scat);
+    return cudaGetLastError();
+}
+
+cudaError_t tape_kinetic_launch(cudaStream_t st, int grid, const TapeDev& T, long long n, double mass, double* part) {
+    k_tape_kinetic<<<grid, TAPE_NT, 0, st>>>(T, n, mass, part);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t tape_from_store_launch(cudaStream_t st, int nsm, const PStore<R>& ps, const long long* n_cur,
+                                   const TapeDev& T, double* w_out, long long nid) {
+    k_tape_from_store<R><<<nsm * 8, TAPE_NT, 0, st>>>(ps, n_cur, T, w_out, nid);
+    return cudaGetLastError();
+}
+template cudaError_t tape_from_store_launch<double>(cudaStream_t, int, const PStore<double>&, const long long*,
+                                                    const TapeDev&, double*, long long);
+template cudaError_t tape_from_store_launch<float>(cudaStream_t, int, const PStore<float>&, const long long*,
+                                                   const TapeDev&, double*, long long);
+
+cudaError_t tape_to_phys_launch(cudaStream_t st, const TapeDev& T, long long n, const GridDev& g, double* const* out) {
+    if (n > 0) k_tape_to_phys<<<pgrid(n), TAPE_NT, 0, st>>>(T, n, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t lam_to_phys_launch(cudaStream_t st, const LamDev& L, long long n, const GridDev& g, double* const* out) {
+    if (n > 0) k_lam_to_phys<<<pgrid(n), TAPE_NT, 0, st>>>(L, n, g, out);
+    return cudaGetLastError();
+}
+
+// One adjoint field step on L = (lE, lB) (padded), producing LJ.
+cudaError_t adj_fields_launch(cudaStream_t st, double* L, double* LJ, const GridDev& g) {
+    const dim3 gr = agrid(g), bl(AF_BX, AF_BY);
+    const double h = 0.5 * g.dt;
+    k_adj_mask_fill<<<gr, bl, 0, st>>>(L, g, 3);           // lB' = M_B lB1
+    k_adj_curlB<<<gr, bl, 0, st>>>(L, g, -h);              // lE1 -= h C_B lB'
+    k_adj_mask_fill<<<gr, bl, 0, st>>>(L, g, 0);           // lE^n = M_E lE1
+    k_adj_curlE<<<gr, bl, 0, st>>>(L, LJ, g, g.dt, -g.dt);  // lB' += dt C_E lE^n, lJ = -dt lE^n
+    k_adj_mask_fill<<<gr, bl, 0, st>>>(L, g, 3);           // lB^n = M_B lB'
+    k_adj_curlB<<<gr, bl, 0, st>>>(L, g, -h);              // lE^n -= h C_B lB^n
+    return cudaGetLastError();
+}
+
+cudaError_t adj_fold_add_launch(cudaStream_t st, double* L, double* scat, const GridDev& g) {
+    k_adj_fold_add<<<agrid(g), dim3(AF_BX, AF_BY), 0, st>>>(L, scat, g);
+    return cudaGetLastError();
+}
+
+}  // namespace picgb

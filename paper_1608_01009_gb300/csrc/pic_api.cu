@@ -34,6 +34,20 @@ template <class R>
 cudaError_t kinetic_launch(cudaStream_t, int, const PStore<R>&, const long long*, double, double*);
 cudaError_t energy_finalize_launch(cudaStream_t, const double*, int, const double*, int, double, double*);
 
+// differentiable path (k_adjoint.cu)
+cudaError_t tape_step_launch(cudaStream_t, const TapeDev&, long long, const StepParams&, const double*, double*);
+cudaError_t tape_seed_launch(cudaStream_t, const TapeDev&, const LamDev&, long long, double, double);
+cudaError_t tape_adjoint_launch(cudaStream_t, const TapeDev&, const LamDev&, long long, const StepParams&,
+                                const double*, const double*, double*);
+cudaError_t tape_kinetic_launch(cudaStream_t, int, const TapeDev&, long long, double, double*);
+template <class R>
+cudaError_t tape_from_store_launch(cudaStream_t, int, const PStore<R>&, const long long*, const TapeDev&, double*,
+                                   long long);
+cudaError_t tape_to_phys_launch(cudaStream_t, const TapeDev&, long long, const GridDev&, double* const*);
+cudaError_t lam_to_phys_launch(cudaStream_t, const LamDev&, long long, const GridDev&, double* const*);
+cudaError_t adj_fields_launch(cudaStream_t, double*, double*, const GridDev&);
+cudaError_t adj_fold_add_launch(cudaStream_t, double*, double*, const GridDev&);
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -57,7 +71,41 @@ struct Species {
     int* d_nchunks = nullptr;
     double* d_ek = nullptr;        // kinetic-energy partials of the last push (push_grid entries)
     double* d_stage = nullptr;     // 7 x cap FP64 staging area for host uploads (allocated on first use)
+    long long nid = 0;             // ids 0..nid-1 were given at the last load
     std::vector<void*> allocs;
+};
+
+// Recorded differentiable run: id-ordered FP64 particle states of every
+// species, checkpoints every K steps, per-step states of the segment being
+// reversed, and the cotangent buffers.
+struct TapeSpecies {
+    long long n = 0;
+    double* w = nullptr;
+    TapeDev cur{};
+    LamDev lam{};
+    std::vector<TapeDev> ck, snap;
+};
+
+struct Tape {
+    bool ready = false;
+    int nsteps = 0, K = 1;
+    std::vector<TapeSpecies> sp;
+    std::vector<double*> ckEB, snapEB;
+    double* finalEB = nullptr;
+    double* L = nullptr;     // cotangents of E, B (6 padded components)
+    double* LJ = nullptr;    // cotangent of J (3 padded components, ghosts filled)
+    double* scat = nullptr;  // gather cotangents scattered by the particles (6 padded)
+    double* stage = nullptr; // 7 x n FP64 staging to re-load the store
+    std::vector<void*> allocs;
+    void release() {
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+        sp.clear();
+        ckEB.clear();
+        snapEB.clear();
+        finalEB = L = LJ = scat = stage = nullptr;
+        ready = false;
+    }
 };
 
 }  // namespace picgb
@@ -96,6 +144,7 @@ struct pic_ctx {
     double stage_ms[4] = {0, 0, 0, 0};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
     std::vector<void*> allocs;
+    Tape tape;
 };
 
 namespace {
@@ -344,6 +393,7 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
         for (int k = 0; k < 7; ++k) dsrc[k] = src[k];
     }
     long long nn = n;
+    s.nid = n;
     CUDA_TRY(c, cudaMemcpyAsync(s.d_n, &nn, sizeof(long long), cudaMemcpyHostToDevice, c->st));
     cudaError_t e = c->mixed ? load_launch<float>(c->st, n, dsrc, s.s32.a(), c->g)
                              : load_launch<double>(c->st, n, dsrc, s.s64.a(), c->g);
@@ -522,6 +572,219 @@ int finalize_energy(pic_ctx* c, int nwf) {
     return PIC_OK;
 }
 
+
+// ---------------------------------------------------------------- differentiable runs
+StepParams step_params(const pic_ctx* c, const Species& s) {
+    StepParams sp;
+    sp.g = c->g;
+    sp.qdt2m = 0.5 * s.q * c->g.dt / s.m;
+    for (int a = 0; a < 3; ++a) {
+        sp.dtd[a] = c->g.dt / c->g.d[a];
+        sp.cq[a] = s.q / (c->g.dt * c->g.d[(a + 1) % 3] * c->g.d[(a + 2) % 3]);
+    }
+    sp.mass = s.m;
+    return sp;
+}
+
+int alloc_tape_dev(pic_ctx* c, Tape& t, TapeDev& d, long long n, const double* w) {
+    int r = PIC_OK;
+    for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &d.xi[a], (size_t)n);
+    for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &d.u[a], (size_t)n);
+    if (!r) r = dalloc(c, t.allocs, &d.act, (size_t)n);
+    d.w = w;
+    return r;
+}
+
+int copy_tape_dev(pic_ctx* c, const TapeDev& dst, const TapeDev& src, long long n) {
+    if (n <= 0) return PIC_OK;
+    for (int a = 0; a < 3; ++a) {
+        CUDA_TRY(c, cudaMemcpyAsync(dst.xi[a], src.xi[a], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(dst.u[a], src.u[a], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(dst.act, src.act, n * sizeof(int), cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
+int copy_EB(pic_ctx* c, double* dst, const double* src) {
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, 6 * c->g.P * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
+// One whole step of the differentiable path on the context's fields.
+int tape_step(pic_ctx* c) {
+    Tape& t = c->tape;
+    for (size_t i = 0; i < c->sp.size(); ++i) {
+        const StepParams sp = step_params(c, c->sp[i]);
+        CUDA_TRY(c, tape_step_launch(c->st, t.sp[i].cur, t.sp[i].n, sp, c->EB, c->J));
+        c->launches += t.sp[i].n > 0 ? 1 : 0;
+    }
+    const double h = 0.5 * c->g.dt;
+    CUDA_TRY(c, fdtd_b_launch(c->st, c->EB, c->g, h, 0, nullptr, nullptr));
+    CUDA_TRY(c, fdtd_e_launch(c->st, c->EB, c->J, c->Jlast, c->g));
+    CUDA_TRY(c, fdtd_b_launch(c->st, c->EB, c->g, h, 1, c->EB32, c->d_wf));
+    c->launches += 3;
+    return PIC_OK;
+}
+
+int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
+    if (nsteps < 1 || K < 1) return fail(c, PIC_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+    Tape& t = c->tape;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    t.release();
+    t.nsteps = nsteps;
+    t.K = K;
+    const int nck = (nsteps + K - 1) / K;
+    const int nsnap = K < nsteps ? K : nsteps;
+    const long long P6 = 6 * c->g.P;
+    int r = PIC_OK;
+    long long nmax = 1;
+    t.sp.resize(c->sp.size());
+    for (size_t i = 0; i < c->sp.size() && !r; ++i) {
+        TapeSpecies& ts = t.sp[i];
+        Species& s = c->sp[i];
+        ts.n = s.nid;
+        nmax = ts.n > nmax ? ts.n : nmax;
+        r = dalloc(c, t.allocs, &ts.w, (size_t)(ts.n > 0 ? ts.n : 1));
+        if (!r) r = alloc_tape_dev(c, t, ts.cur, ts.n, ts.w);
+        for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &ts.lam.xi[a], (size_t)ts.n);
+        for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &ts.lam.u[a], (size_t)ts.n);
+        ts.ck.resize(nck);
+        ts.snap.resize(nsnap);
+        for (int k = 0; k < nck && !r; ++k) r = alloc_tape_dev(c, t, ts.ck[k], ts.n, ts.w);
+        for (int k = 0; k < nsnap && !r; ++k) r = alloc_tape_dev(c, t, ts.snap[k], ts.n, ts.w);
+        if (r) break;
+        // the current (binned) store -> id order
+        if (ts.n > 0) {
+            CUDA_TRY(c, cudaMemsetAsync(ts.cur.act, 0, ts.n * sizeof(int), c->st));
+            CUDA_TRY(c, cudaMemsetAsync(ts.w, 0, ts.n * sizeof(double), c->st));
+            for (int a = 0; a < 3; ++a) {
+                CUDA_TRY(c, cudaMemsetAsync(ts.cur.xi[a], 0, ts.n * sizeof(double), c->st));
+                CUDA_TRY(c, cudaMemsetAsync(ts.cur.u[a], 0, ts.n * sizeof(double), c->st));
+            }
+            cudaError_t e = c->mixed ? tape_from_store_launch<float>(c->st, c->nsm, s.s32.a(), s.d_n, ts.cur, ts.w, ts.n)
+                                     : tape_from_store_launch<double>(c->st, c->nsm, s.s64.a(), s.d_n, ts.cur, ts.w,
+                                                                      ts.n);
+            c->launches += 1;
+            if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "tape load: %s", cudaGetErrorString(e));
+        }
+    }
+    t.ckEB.resize(nck);
+    t.snapEB.resize(nsnap);
+    for (int k = 0; k < nck && !r; ++k) r = dalloc(c, t.allocs, &t.ckEB[k], (size_t)P6);
+    for (int k = 0; k < nsnap && !r; ++k) r = dalloc(c, t.allocs, &t.snapEB[k], (size_t)P6);
+    if (!r) r = dalloc(c, t.allocs, &t.finalEB, (size_t)P6);
+    if (!r) r = dalloc(c, t.allocs, &t.L, (size_t)P6);
+    if (!r) r = dalloc(c, t.allocs, &t.LJ, (size_t)(3 * c->g.P));
+    if (!r) r = dalloc(c, t.allocs, &t.scat, (size_t)P6);
+    if (!r) r = dalloc(c, t.allocs, &t.stage, (size_t)(7 * nmax));
+    if (r) {
+        t.release();
+        return r;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        if (n % K == 0) {
+            const int k = n / K;
+            for (auto& ts : t.sp)
+                if ((r = copy_tape_dev(c, ts.ck[k], ts.cur, ts.n))) return r;
+            if ((r = copy_EB(c, t.ckEB[k], c->EB))) return r;
+        }
+        if ((r = tape_step(c))) return r;
+    }
+    if ((r = copy_EB(c, t.finalEB, c->EB))) return r;
+    // final kinetic energy (and field energy, from the last B half step)
+    for (size_t i = 0; i < c->sp.size(); ++i)
+        CUDA_TRY(c, tape_kinetic_launch(c->st, c->push_grid, t.sp[i].cur, t.sp[i].n, c->sp[i].m, c->sp[i].d_ek));
+    c->launches += c->sp.size();
+    if ((r = finalize_energy(c, fdtd_blocks(c->g)))) return r;
+    double out[2];
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->d_energy, sizeof out, cudaMemcpyDeviceToHost, c->st));
+    // the context continues from the final state: re-load the binned store
+    for (size_t i = 0; i < c->sp.size(); ++i) {
+        TapeSpecies& ts = t.sp[i];
+        if (ts.n == 0) continue;
+        double* dst[7];
+        for (int k = 0; k < 7; ++k) dst[k] = t.stage + (size_t)k * ts.n;
+        double** ddst = nullptr;
+        CUDA_TRY(c, cudaMalloc(&ddst, sizeof dst));
+        cudaError_t e = cudaMemcpyAsync(ddst, dst, sizeof dst, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = tape_to_phys_launch(c->st, ts.cur, ts.n, c->g, ddst);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        cudaFree(ddst);
+        if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "tape write-back: %s", cudaGetErrorString(e));
+        c->launches += 1;
+        const double* src[7] = {dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6]};
+        if ((r = load_particles(c, c->sp[i], ts.n, src, true))) return r;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    c->energy_fresh = false;
+    c->since_sort = 0;
+    c->steps += nsteps;
+    t.ready = true;
+    if (wk) *wk = out[1];
+    return device_status(c);
+}
+
+int tape_backward_impl(pic_ctx* c, double wk_weight, const double* const gE[3], const double* const gB[3],
+                       double* const dE0[3], double* const dB0[3]) {
+    Tape& t = c->tape;
+    if (!t.ready) return fail(c, PIC_ERR_STATE, "no tape recorded (call pic_tape_forward first)");
+    const long long P6 = 6 * c->g.P;
+    CUDA_TRY(c, cudaMemsetAsync(t.L, 0, P6 * sizeof(double), c->st));
+    CUDA_TRY(c, cudaMemsetAsync(t.LJ, 0, 3 * c->g.P * sizeof(double), c->st));
+    CUDA_TRY(c, cudaMemsetAsync(t.scat, 0, P6 * sizeof(double), c->st));
+    for (int k = 0; k < 6; ++k) {
+        const double* src = k < 3 ? (gE ? gE[k] : nullptr) : (gB ? gB[k - 3] : nullptr);
+        if (!src) continue;
+        cudaMemcpy3DParms p = copy_params(c->g, t.L + k * c->g.P, const_cast<double*>(src), true);
+        CUDA_TRY(c, cudaMemcpy3DAsync(&p, c->st));
+    }
+    // seed: cotangent of the final kinetic energy
+    for (size_t i = 0; i < c->sp.size(); ++i) {
+        CUDA_TRY(c, tape_seed_launch(c->st, t.sp[i].cur, t.sp[i].lam, t.sp[i].n, c->sp[i].m, wk_weight));
+        c->launches += 1;
+    }
+    const int nck = (t.nsteps + t.K - 1) / t.K;
+    int r;
+    for (int k = nck - 1; k >= 0; --k) {
+        const int n0 = k * t.K, n1 = n0 + t.K < t.nsteps ? n0 + t.K : t.nsteps;
+        // restore the checkpoint and replay the segment, keeping each step's state
+        for (auto& ts : t.sp)
+            if ((r = copy_tape_dev(c, ts.cur, ts.ck[k], ts.n))) return r;
+        if ((r = copy_EB(c, c->EB, t.ckEB[k]))) return r;
+        for (int m = 0; m < n1 - n0; ++m) {
+            for (auto& ts : t.sp)
+                if ((r = copy_tape_dev(c, ts.snap[m], ts.cur, ts.n))) return r;
+            if ((r = copy_EB(c, t.snapEB[m], c->EB))) return r;
+            if (m + 1 < n1 - n0 && (r = tape_step(c))) return r;
+        }
+        // adjoint steps, last to first
+        for (int m = n1 - n0 - 1; m >= 0; --m) {
+            CUDA_TRY(c, adj_fields_launch(c->st, t.L, t.LJ, c->g));
+            c->launches += 6;
+            for (size_t i = 0; i < c->sp.size(); ++i) {
+                const StepParams sp = step_params(c, c->sp[i]);
+                CUDA_TRY(c, tape_adjoint_launch(c->st, t.sp[i].snap[m], t.sp[i].lam, t.sp[i].n, sp, t.snapEB[m],
+                                                t.LJ, t.scat));
+                c->launches += 1;
+            }
+            CUDA_TRY(c, adj_fold_add_launch(c->st, t.L, t.scat, c->g));
+            c->launches += 1;
+        }
+    }
+    for (int k = 0; k < 6; ++k) {
+        double* dst = k < 3 ? (dE0 ? dE0[k] : nullptr) : (dB0 ? dB0[k - 3] : nullptr);
+        if (!dst) continue;
+        cudaMemcpy3DParms p = copy_params(c->g, t.L + k * c->g.P, dst, false);
+        CUDA_TRY(c, cudaMemcpy3DAsync(&p, c->st));
+    }
+    // the context's fields return to the end of the tape
+    if ((r = copy_EB(c, c->EB, t.finalEB))) return r;
+    CUDA_TRY(c, refresh_launch(c->st, c->EB, c->g, c->EB32));
+    c->launches += 1;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return device_status(c);
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -612,6 +875,7 @@ int pic_destroy(pic_ctx* c) {
     cudaSetDevice(c->dev);
     cudaStreamSynchronize(c->st);
     for (auto& s : c->sp) free_species(s);
+    c->tape.release();
     for (void* p : c->allocs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -818,4 +1082,39 @@ int pic_launch_count(pic_ctx* c, int64_t* n, int reset) {
     return PIC_OK;
 }
 
+int pic_tape_forward(pic_ctx* c, int nsteps, int ckpt_every, double* wk) {
+    if (!c) return PIC_ERR_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    return tape_forward_impl(c, nsteps, ckpt_every, wk);
+}
+
+int pic_tape_backward(pic_ctx* c, double wk_weight, const double* const gE[3], const double* const gB[3],
+                      double* const dE0[3], double* const dB0[3]) {
+    if (!c) return PIC_ERR_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    return tape_backward_impl(c, wk_weight, gE, gB, dE0, dB0);
+}
+
+int pic_tape_particle_grad(pic_ctx* c, int species, double* const dP[6]) {
+    if (!c) return PIC_ERR_ARG;
+    if (!dP) return fail(c, PIC_ERR_ARG, "null output");
+    if (!c->tape.ready) return fail(c, PIC_ERR_STATE, "no tape recorded");
+    if (species < 0 || species >= (int)c->tape.sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    TapeSpecies& ts = c->tape.sp[species];
+    if (ts.n == 0) return PIC_OK;
+    double** d = nullptr;
+    CUDA_TRY(c, cudaMalloc(&d, 6 * sizeof(double*)));
+    double* h[6];
+    for (int k = 0; k < 6; ++k) h[k] = dP[k];
+    cudaError_t e = cudaMemcpyAsync(d, h, sizeof h, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = lam_to_phys_launch(c->st, ts.lam, ts.n, c->g, d);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    cudaFree(d);
+    c->launches += 1;
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "particle grad: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
 }  // extern "C"
+

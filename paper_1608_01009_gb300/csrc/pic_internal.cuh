@@ -74,6 +74,25 @@ struct PushParams {
     float qdt2m_f, dtd_f[3], cq_f[3];
 };
 
+// Differentiable path: id-ordered FP64 particle state, its cotangents, and the
+// per-species step constants.
+struct TapeDev {
+    double* xi[3];  // position in cells
+    double* u[3];
+    const double* w;
+    int* act;       // 1 active; 0 deactivated at an absorbing boundary, or absent
+};
+
+struct LamDev {
+    double* xi[3];  // cotangent of the position (in cells)
+    double* u[3];   // cotangent of the momentum
+};
+
+struct StepParams {
+    GridDev g;
+    double qdt2m, dtd[3], cq[3], mass;
+};
+
 constexpr int CHUNK = 4096;  // most particles of one supercell handled by one CTA pass
 
 __host__ __device__ inline int pack_cell(int ix, int iy, int iz) { return ix | (iy << 10) | (iz << 20); }

@@ -70,6 +70,9 @@ SIGNATURES = {
     "pic_stage_times": [_VP, C.POINTER(C.c_double * 4)],
     "pic_launch_count": [_VP, C.POINTER(C.c_int64), C.c_int],
     "pic_field_energy_noalloc": [_P3, _P3, C.POINTER(C.c_int32 * 3), C.POINTER(C.c_double * 3), _VP, _VP],
+    "pic_tape_forward": [_VP, C.c_int, C.c_int, C.POINTER(C.c_double)],
+    "pic_tape_backward": [_VP, C.c_double, _VP, _VP, _VP, _VP],
+    "pic_tape_particle_grad": [_VP, C.c_int, _VP],
 }
 
 
@@ -183,6 +186,7 @@ class Simulation:
         if dev:
             self.stream.synchronize()
         self.nspecies += 1
+        self._tape_ids = getattr(self, "_tape_ids", []) + [n]
         return sid.value
 
     def set_particles(self, species, x, y, z, ux, uy, uz, w):
@@ -193,6 +197,7 @@ class Simulation:
         n = int(arrs[0].shape[0])
         f = self.lib.pic_set_particles_dev if dev else self.lib.pic_set_particles
         self._check(f(self.ctx, int(species), n, *[_ptr(a) for a in arrs]))
+        self._tape_ids[int(species)] = n
 
     def count(self, species=0) -> int:
         n = C.c_int64()
@@ -272,6 +277,46 @@ class Simulation:
         out = (C.c_double * 4)()
         self._check(self.lib.pic_stage_times(self.ctx, C.byref(out)))
         return dict(push_deposit=out[0], field=out[1], sort=out[2], diagnostics=out[3])
+
+    # ------------------------------------------------------------------ differentiable runs
+    def tape_forward(self, nsteps, ckpt_every) -> float:
+        """Advance nsteps on the differentiable FP64 path, checkpointing every
+        ckpt_every steps; returns the final kinetic energy W_K."""
+        wk = C.c_double()
+        self._check(self.lib.pic_tape_forward(self.ctx, int(nsteps), int(ckpt_every), C.byref(wk)))
+        return wk.value
+
+    def tape_backward(self, wk_weight=1.0, gE=None, gB=None):
+        """Gradient of wk_weight * W_K + <gE, E_final> + <gB, B_final> with respect
+        to the fields at the start of the tape: (dE0, dB0) torch tensors."""
+        t = self.torch
+        shape = (3, self.n[2], self.n[1], self.n[0])
+        dE = t.zeros(shape, dtype=t.float64, device=self.device)
+        dB = t.zeros(shape, dtype=t.float64, device=self.device)
+        keep = []
+
+        def arr(F):
+            if F is None:
+                return None
+            F = F.contiguous() if not isinstance(F, np.ndarray) else t.as_tensor(F, device=self.device)
+            keep.append(F)
+            a = _P3(*[F[c].data_ptr() for c in range(3)])
+            keep.append(a)
+            return C.addressof(a)
+
+        self.stream.synchronize()
+        self._check(self.lib.pic_tape_backward(self.ctx, float(wk_weight), arr(gE), arr(gB), arr(dE), arr(dB)))
+        return dE, dB
+
+    def tape_particle_grad(self, species=0, n=None):
+        """dL/d(x, y, z, ux, uy, uz) of the tape's starting particles, in id order."""
+        t = self.torch
+        if n is None:
+            n = self._tape_ids[species]
+        out = [t.zeros(n, dtype=t.float64, device=self.device) for _ in range(6)]
+        ptrs = (_VP * 6)(*[o.data_ptr() for o in out])
+        self._check(self.lib.pic_tape_particle_grad(self.ctx, int(species), C.addressof(ptrs)))
+        return dict(zip(("x", "y", "z", "ux", "uy", "uz"), out))
 
     def launch_count(self, reset=False) -> int:
         n = C.c_int64()
