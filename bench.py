@@ -223,6 +223,43 @@ def time_e2e(torch, pic, wl, sim, steps):
     return dict(seconds=dt, npart=wl.nparticles, steps=steps, h2d=h2d, d2h=d2h)
 
 
+def time_adjoint(torch, pic, W, nsteps=200, ckpt=20):
+    """Cost of the differentiable run on the laser-slab workload: the
+    checkpointed forward (pic_tape_forward) and the backward (segment replay +
+    adjoint kernels, pic_tape_backward), against the same steps of pic_step."""
+    wl = W.config("c4")
+    warm = pic.Simulation.from_workload(wl)
+    warm.tape_forward(ckpt, ckpt)
+    warm.tape_backward(1.0)
+    warm.step(3)
+    warm.close()
+    sim = pic.Simulation.from_workload(wl)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    wk = sim.tape_forward(nsteps, ckpt)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    dE, dB = sim.tape_backward(1.0)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    sim.close()
+    fast = pic.Simulation.from_workload(wl)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    fast.step(nsteps)
+    fast.sync()
+    t4 = time.perf_counter()
+    fast.close()
+    fwd, bwd, fst = (t1 - t0) * 1e3, (t2 - t1) * 1e3, (t4 - t3) * 1e3
+    return {"workload": "c4: 32x32x64, x/y periodic, z absorbing, slab z in [24,40) cells at 0.1 n_crit, "
+                        "16 e-/cell (%d particles), a0 = 1 plane wave, FP64" % wl.nparticles,
+            "steps": nsteps, "checkpoint_every": ckpt, "loss": "W_K after %d steps" % nsteps,
+            "loss_value": wk, "tape_forward_ms": fwd, "backward_ms": bwd, "fast_forward_ms": fst,
+            "adjoint_forward_ratio": bwd / fwd, "adjoint_vs_fast_forward": bwd / fst,
+            "note": "backward = segment replay (recomputation) + adjoint kernels; ratio against the "
+                    "checkpointed forward of the same differentiable path"}
+
+
 def cpu_oracle_rate(wl, nsteps=1, sample_every=1):
     """The FP64 oracle as it stands (single thread) on the workload state,
     optionally on every k-th particle; returns (particle-steps/s, particles, seconds)."""
@@ -326,6 +363,8 @@ def run_gpu(args):
                         "stage_ms_per_step": {k: round(v, 4) for k, v in r3["stage_ms"].items()},
                         "gpu_launches": r3["launches"], "clocks": clk3.summary()}
         r3["sim"].close()
+    if not args.no_adjoint:
+        out["adjoint"] = time_adjoint(torch, pic, W)
     if not args.no_replica:
         wlr = W.config("r")
         rr = time_gpu(torch, pic, wlr, "fp64", args.steps, args.warmup, with_timing=False)
@@ -360,6 +399,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-replica", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -28,6 +28,20 @@ namespace picgb {
 
 constexpr int TAPE_NT = 256;
 
+// Thread -> particle map of the per-particle kernels: lane l of warp-row r
+// takes particle l * rows + r.  Id order is usually cell order (a cell's
+// particles are consecutive), so this spreads the 32 lanes of a warp over 32
+// distant particles and keeps their atomics off the same grid nodes; the
+// differentiable state of a run this size sits in L2, so the scattered loads
+// are cheap.
+__device__ __forceinline__ long long lane_strided(long long n, bool& ok) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long rows = (n + 31) / 32;
+    const long long p = (t & 31) * rows + (t >> 5);
+    ok = (t >> 5) < rows && p < n;
+    return p;
+}
+
 __device__ __forceinline__ double stag(int comp, int axis, bool magnetic) {
     return magnetic ? (comp == axis ? 0.0 : 0.5) : (comp == axis ? 0.5 : 0.0);
 }
@@ -279,8 +293,9 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
 // One forward step of every particle.
 __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, StepParams sp, const double* __restrict__ EB,
                                                       double* __restrict__ J) {
-    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
-    if (p >= n || !T.act[p]) return;
+    bool ok;
+    const long long p = lane_strided(n, ok);
+    if (!ok || !T.act[p]) return;
     const GridDev& g = sp.g;
     double xi[3] = {T.xi[0][p], T.xi[1][p], T.xi[2][p]};
     double u[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
@@ -339,21 +354,34 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_seed(TapeDev T, LamDev L, long
 // L holds the cotangents of x^{n+1}, u^{n+1/2} on entry and of x^n, u^{n-1/2}
 // on exit; EB = E^n, B^n; LJ = lambda_J (ghosts filled); scat receives the
 // gather cotangents lambda_E, lambda_B (padded, atomics; ghosts folded later).
-__global__ void __launch_bounds__(TAPE_NT) k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp,
+__global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp,
                                                          const double* __restrict__ EB, const double* __restrict__ LJ,
                                                          double* __restrict__ scat) {
-    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
-    if (p >= n || !T.act[p]) return;  // inactive: the step is the identity
+    bool ok;
+    const long long p = lane_strided(n, ok);
+    if (!ok || !T.act[p]) return;  // inactive: the step is the identity
     const GridDev& g = sp.g;
     const double xi[3] = {T.xi[0][p], T.xi[1][p], T.xi[2][p]};
     const double u0[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
-    // recompute the forward step
-    double F[6], fr[6][3], vv[6][8];
+    // recompute the forward gather, with the position derivatives of each
+    // interpolant from the same lerp tree: v = lerp_z(lerp_y(lerp_x(corners)))
+    double F[6], dF[6][3], fr[6][3];
     int bs[6][3];
     for (int c = 0; c < 6; ++c) {
+        double v[8];
         lattice(c, xi, bs[c], fr[c]);
-        corners(EB, g, c, bs[c], vv[c]);
-        F[c] = tri_val(vv[c], fr[c]);
+        corners(EB, g, c, bs[c], v);
+        const double* f = fr[c];
+        const double a0 = v[1] - v[0], a1 = v[3] - v[2], a2 = v[5] - v[4], a3 = v[7] - v[6];
+        const double c00 = fma(f[0], a0, v[0]), c10 = fma(f[0], a1, v[2]);
+        const double c01 = fma(f[0], a2, v[4]), c11 = fma(f[0], a3, v[6]);
+        const double e0 = c10 - c00, e1 = c11 - c01;
+        const double c0 = fma(f[1], e0, c00), c1 = fma(f[1], e1, c01);
+        const double b0 = fma(f[1], a1 - a0, a0), b1 = fma(f[1], a3 - a2, a2);
+        dF[c][2] = c1 - c0;
+        dF[c][1] = fma(f[2], e1 - e0, e0);
+        dF[c][0] = fma(f[2], b1 - b0, b0);
+        F[c] = fma(f[2], dF[c][2], c0);
     }
     double u1[3] = {u0[0], u0[1], u0[2]};
     boris(u1, F, F + 3, sp.qdt2m);
@@ -393,27 +421,21 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_adjoint(TapeDev T, LamDev L, l
     // Boris
     double lu0[3], lF[6] = {0, 0, 0, 0, 0, 0};
     boris_adjoint(u0, F, F + 3, sp.qdt2m, lu1, lu0, lF, lF + 3);
-    // gather: scatter lambda_F with the CIC weights, and the position gradient
+    // gather: scatter lambda_F with the separable CIC weights, and the position gradient
     for (int c = 0; c < 6; ++c) {
         const double* f = fr[c];
-        const double* v = vv[c];
+        const double sc = lF[c];
+        lx0[0] = fma(sc, dF[c][0], lx0[0]);
+        lx0[1] = fma(sc, dF[c][1], lx0[1]);
+        lx0[2] = fma(sc, dF[c][2], lx0[2]);
+        const double gx = 1.0 - f[0], sz0 = sc * (1.0 - f[2]), sz1 = sc * f[2];
+        const double syz[4] = {sz0 * (1.0 - f[1]), sz0 * f[1], sz1 * (1.0 - f[1]), sz1 * f[1]};
         double* S = scat + (long long)c * g.P;
-        for (int q = 0; q < 8; ++q) {
-            const int bx = q & 1, by = (q >> 1) & 1, bz = q >> 2;
-            const double wq = (bx ? f[0] : 1 - f[0]) * (by ? f[1] : 1 - f[1]) * (bz ? f[2] : 1 - f[2]);
-            atomicAdd(&S[pidx(g, bs[c][0] + bx, bs[c][1] + by, bs[c][2] + bz)], lF[c] * wq);
+        for (int q = 0; q < 4; ++q) {
+            const long long o = pidx(g, bs[c][0], bs[c][1] + (q & 1), bs[c][2] + (q >> 1));
+            atomicAdd(&S[o], syz[q] * gx);
+            atomicAdd(&S[o + 1], syz[q] * f[0]);
         }
-        double dfx = 0.0, dfy = 0.0, dfz = 0.0;
-        for (int q = 0; q < 8; ++q) {
-            const int bx = q & 1, by = (q >> 1) & 1, bz = q >> 2;
-            const double wx = bx ? f[0] : 1 - f[0], wy = by ? f[1] : 1 - f[1], wz = bz ? f[2] : 1 - f[2];
-            dfx += (bx ? 1.0 : -1.0) * wy * wz * v[q];
-            dfy += (by ? 1.0 : -1.0) * wx * wz * v[q];
-            dfz += (bz ? 1.0 : -1.0) * wx * wy * v[q];
-        }
-        lx0[0] += lF[c] * dfx;
-        lx0[1] += lF[c] * dfy;
-        lx0[2] += lF[c] * dfz;
     }
     for (int c = 0; c < 3; ++c) {
         L.xi[c][p] = lx0[c];
@@ -594,20 +616,35 @@ __global__ void k_adj_fold_add(double* __restrict__ L, double* __restrict__ scat
     int i, j, k;
     if (!acell(g, i, j, k)) return;
     const long long o = pidx(g, i, j, k);
+    int ix[2], iy[2], iz[2], cx, cy, cz;
+    bool fx[2], fy[2], fz[2];
+    img(i, g.n[0], g.bc[0], ix, fx, cx);
+    img(j, g.n[1], g.bc[1], iy, fy, cy);
+    img(k, g.n[2], g.bc[2], iz, fz, cz);
+    double s[6];
     for (int c = 0; c < 6; ++c) {
-        double* S = scat + (long long)c * g.P;
-        double s = 0.0;
-        for_images(g, i, j, k, false, [&](long long q, bool fold, bool) {
-            if (fold) s += S[q];
-            S[q] = 0.0;
-        });
-        L[(long long)c * g.P + o] += s;
+        s[c] = scat[(long long)c * g.P + o];
+        scat[(long long)c * g.P + o] = 0.0;
     }
+    if (cx * cy * cz > 1) {
+        for (int c3 = 0; c3 < cz; ++c3)
+            for (int b3 = 0; b3 < cy; ++b3)
+                for (int a3 = 0; a3 < cx; ++a3) {
+                    if ((a3 | b3 | c3) == 0) continue;
+                    const long long q = pidx(g, ix[a3], iy[b3], iz[c3]);
+                    const bool f = fx[a3] && fy[b3] && fz[c3];
+                    for (int c = 0; c < 6; ++c) {
+                        if (f) s[c] += scat[(long long)c * g.P + q];
+                        scat[(long long)c * g.P + q] = 0.0;
+                    }
+                }
+    }
+    for (int c = 0; c < 6; ++c) L[(long long)c * g.P + o] += s[c];
 }
 
 // ------------------------------------------------------------------ launchers
 static dim3 agrid(const GridDev& g) { return dim3((g.n[0] + AF_BX - 1) / AF_BX, (g.n[1] + AF_BY - 1) / AF_BY, g.n[2]); }
-static int pgrid(long long n) { return (int)((n + TAPE_NT - 1) / TAPE_NT); }
+static int pgrid(long long n) { return (int)((32 * ((n + 31) / 32) + TAPE_NT - 1) / TAPE_NT); }
 
 cudaError_t tape_step_launch(cudaStream_t st, const TapeDev& T, long long n, const StepParams& sp, const double* EB,
                              double* J) {

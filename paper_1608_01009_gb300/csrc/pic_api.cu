@@ -89,6 +89,7 @@ struct TapeSpecies {
 struct Tape {
     bool ready = false;
     int nsteps = 0, K = 1;
+    int snap_seg = -1;  // checkpoint segment whose per-step states `snap` holds (-1: none)
     std::vector<TapeSpecies> sp;
     std::vector<double*> ckEB, snapEB;
     double* finalEB = nullptr;
@@ -105,6 +106,7 @@ struct Tape {
         snapEB.clear();
         finalEB = L = LJ = scat = stage = nullptr;
         ready = false;
+        snap_seg = -1;
     }
 };
 
@@ -688,8 +690,16 @@ int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
                 if ((r = copy_tape_dev(c, ts.ck[k], ts.cur, ts.n))) return r;
             if ((r = copy_EB(c, t.ckEB[k], c->EB))) return r;
         }
+        if (n / K == nck - 1) {
+            // the last segment's per-step states are kept: the backward starts there without a replay
+            const int m = n - (nck - 1) * K;
+            for (auto& ts : t.sp)
+                if ((r = copy_tape_dev(c, ts.snap[m], ts.cur, ts.n))) return r;
+            if ((r = copy_EB(c, t.snapEB[m], c->EB))) return r;
+        }
         if ((r = tape_step(c))) return r;
     }
+    t.snap_seg = nck - 1;
     if ((r = copy_EB(c, t.finalEB, c->EB))) return r;
     // final kinetic energy (and field energy, from the last B half step)
     for (size_t i = 0; i < c->sp.size(); ++i)
@@ -747,15 +757,18 @@ int tape_backward_impl(pic_ctx* c, double wk_weight, const double* const gE[3], 
     int r;
     for (int k = nck - 1; k >= 0; --k) {
         const int n0 = k * t.K, n1 = n0 + t.K < t.nsteps ? n0 + t.K : t.nsteps;
-        // restore the checkpoint and replay the segment, keeping each step's state
-        for (auto& ts : t.sp)
-            if ((r = copy_tape_dev(c, ts.cur, ts.ck[k], ts.n))) return r;
-        if ((r = copy_EB(c, c->EB, t.ckEB[k]))) return r;
-        for (int m = 0; m < n1 - n0; ++m) {
+        if (t.snap_seg != k) {
+            // restore the checkpoint and replay the segment, keeping each step's state
             for (auto& ts : t.sp)
-                if ((r = copy_tape_dev(c, ts.snap[m], ts.cur, ts.n))) return r;
-            if ((r = copy_EB(c, t.snapEB[m], c->EB))) return r;
-            if (m + 1 < n1 - n0 && (r = tape_step(c))) return r;
+                if ((r = copy_tape_dev(c, ts.cur, ts.ck[k], ts.n))) return r;
+            if ((r = copy_EB(c, c->EB, t.ckEB[k]))) return r;
+            for (int m = 0; m < n1 - n0; ++m) {
+                for (auto& ts : t.sp)
+                    if ((r = copy_tape_dev(c, ts.snap[m], ts.cur, ts.n))) return r;
+                if ((r = copy_EB(c, t.snapEB[m], c->EB))) return r;
+                if (m + 1 < n1 - n0 && (r = tape_step(c))) return r;
+            }
+            t.snap_seg = k;
         }
         // adjoint steps, last to first
         for (int m = n1 - n0 - 1; m >= 0; --m) {
