@@ -142,12 +142,20 @@ def _dist():
 
 
 def _barrier_max(torch, value, ws):
+    """Maximum of `value` over the ranks (the slowest replica's time)."""
     if ws == 1:
         return value
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.barrier()
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_value(npart_per_rank, ws, steps, ms_max):
+    """Whole-job particle-steps/s: every rank's particles over the slowest rank's time."""
+    return npart_per_rank * ws * steps / (ms_max / 1e3)
 
 
 def _workload_desc(wl, precision):
@@ -319,7 +327,7 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         r = time_gpu(torch, pic, wl, "fp64", args.steps, args.warmup)
     ms = _barrier_max(torch, r["ms"], ws)
-    value = r["npart"] * ws * args.steps / (ms / 1e3)
+    value = weak_value(r["npart"], ws, args.steps, ms)
     push_ms = r["stage_ms"]["push_deposit"]
     flops = FLOPS_PER_PARTICLE * r["npart"]
     bytes_ = BYTES_PER_PARTICLE["fp64"] * r["npart"]

@@ -182,3 +182,17 @@ def test_status_and_launch_count():
     sim.sync()
     # per step: 1 push + 3 field + 1 energy; one sort (5 kernels) at the 4th step (K = 3)
     assert sim.launch_count() == 6 * 5 + 5
+
+
+def test_non_finite_input_is_reported_not_trapped():
+    wl = _plasma((8, 8, 8), 2, vth=0.1, seed=16)
+    sim = PT.make_sim(wl)
+    E = np.array(wl.E)
+    E[0, 3, 3, 3] = np.nan
+    sim.set_fields(E, wl.B)
+    sim.step(2)
+    from paper_1608_01009_gb300 import pic as P
+    with pytest.raises(P.PicError) as ei:
+        sim.energy()
+    assert ei.value.code == -5  # PIC_ERR_NAN
+    sim.close()
