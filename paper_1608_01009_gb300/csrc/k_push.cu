@@ -46,17 +46,37 @@ __device__ __forceinline__ R lerp(R a, R b, R t) {
     return fma(t, b - a, a);
 }
 
-// Shared-memory field tile.  TMA lands the raw (S+4)^3 x 6 box.  For the FP64
-// kernel with S <= 4 it is then re-laid as pairs (F[i], F[i+1]) so that each
-// x-lerp reads one 16-byte vector (4 loads per component instead of 8).  The
-// FP32 kernel keeps the raw tile: its quad layout (4 loads -> 2) cost more in
-// occupancy (3 instead of 4 CTAs per SM) and bank conflicts than it saved.
+// Shared-memory field tile.  TMA lands the raw (S+4)^3 x 6 box.  For S <= 4 it
+// is then rebuilt as per-cell bilinear coefficients of every z plane,
+//   f(a, b) = F00 + a Dx + b (Dy + a Dxy)        (a, b = x, y fractions),
+// over lattice cells i, j in [0, T-2], k in [0, T-1]: one trilinear
+// interpolation is then 2 vector loads and 2 x 3 FMAs + 1 lerp, instead of 8
+// scalar loads and 7 lerps (14 operations).  FP32: one float4 per cell; FP64:
+// two double2.  S = 8 keeps the raw tile (its coefficient tile would not fit).
 template <class R, int S>
 struct Tile {
     static constexpr int T = S + 4, T3 = T * T * T;
-    static constexpr bool kExpand = sizeof(R) == 8 && S <= 4;
-    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    static constexpr int NE = (T - 1) * (T - 1) * T;  // coefficient cells per component
+    static constexpr bool kCoef = S <= 4;
 };
+
+template <class R>
+struct Coef;
+template <>
+struct Coef<float> {
+    float4 v;  // F00, Dx, Dy, Dxy
+};
+template <>
+struct Coef<double> {
+    double2 a, b;  // (F00, Dx), (Dy, Dxy)
+};
+
+__device__ __forceinline__ float bil(const Coef<float>& q, float a, float b) {
+    return fmaf(b, fmaf(a, q.v.w, q.v.z), fmaf(a, q.v.y, q.v.x));
+}
+__device__ __forceinline__ double bil(const Coef<double>& q, double a, double b) {
+    return fma(b, fma(a, q.b.y, q.b.x), fma(a, q.a.y, q.a.x));
+}
 
 template <class R, int T>
 __device__ __forceinline__ R tri_raw(const R* __restrict__ F, int i, int j, int k, R a, R b, R c) {
@@ -68,37 +88,29 @@ __device__ __forceinline__ R tri_raw(const R* __restrict__ F, int i, int j, int 
     return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
 }
 
-template <int T>
-__device__ __forceinline__ float tri_x(const float4* __restrict__ Q, int i, int j, int k, float a, float b, float c) {
-    const float4 p = Q[(k * T + j) * T + i], q = Q[((k + 1) * T + j) * T + i];
-    const float c00 = lerp(p.x, p.y, a), c10 = lerp(p.z, p.w, a);
-    const float c01 = lerp(q.x, q.y, a), c11 = lerp(q.z, q.w, a);
-    return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
+template <class R, int T>
+__device__ __forceinline__ R tri_coef(const Coef<R>* __restrict__ X, int i, int j, int k, R a, R b, R c) {
+    const int o = (k * (T - 1) + j) * (T - 1) + i;
+    const R v0 = bil(X[o], a, b), v1 = bil(X[o + (T - 1) * (T - 1)], a, b);
+    return lerp(v0, v1, c);
 }
 
-template <int T>
-__device__ __forceinline__ double tri_x(const double2* __restrict__ D, int i, int j, int k, double a, double b,
-                                        double c) {
-    const int o = (k * T + j) * T + i;
-    const double2 p0 = D[o], p1 = D[o + T], q0 = D[o + T * T], q1 = D[o + T * T + T];
-    const double c00 = lerp(p0.x, p0.y, a), c10 = lerp(p1.x, p1.y, a);
-    const double c01 = lerp(q0.x, q0.y, a), c11 = lerp(q1.x, q1.y, a);
-    return lerp(lerp(c00, c10, b), lerp(c01, c11, b), c);
-}
-
-// Build the vector tile X from the raw tile F (entries never read by tri_x --
-// the last x (and, for quads, y) plane -- are skipped).
-template <int T, int NT>
-__device__ __forceinline__ void expand_tile(const float* __restrict__ F, float4* __restrict__ X) {
-    for (int e = threadIdx.x; e < 6 * T * T * T; e += NT) {
-        const int i = e % T, j = (e / T) % T;
-        if (i < T - 1 && j < T - 1) X[e] = make_float4(F[e], F[e + 1], F[e + T], F[e + T + 1]);
-    }
-}
-template <int T, int NT>
-__device__ __forceinline__ void expand_tile(const double* __restrict__ F, double2* __restrict__ X) {
-    for (int e = threadIdx.x; e < 6 * T * T * T; e += NT) {
-        if (e % T < T - 1) X[e] = make_double2(F[e], F[e + 1]);
+// Build the coefficient tile X from the raw tile F.
+template <class R, int T, int NT>
+__device__ __forceinline__ void build_coef(const R* __restrict__ F, Coef<R>* __restrict__ X) {
+    constexpr int NE = (T - 1) * (T - 1) * T;
+    for (int e = threadIdx.x; e < 6 * NE; e += NT) {
+        const int comp = e / NE, r = e - comp * NE;
+        const int i = r % (T - 1), j = (r / (T - 1)) % (T - 1), k = r / ((T - 1) * (T - 1));
+        const R* f = F + comp * T * T * T + (k * T + j) * T + i;
+        const R f00 = f[0], f10 = f[1], f01 = f[T], f11 = f[T + 1];
+        const R dx = f10 - f00, dy = f01 - f00, dxy = (f11 - f10) - dy;
+        if constexpr (sizeof(R) == 4) {
+            X[e].v = make_float4(f00, dx, dy, dxy);
+        } else {
+            X[e].a = make_double2(f00, dx);
+            X[e].b = make_double2(dy, dxy);
+        }
     }
 }
 
@@ -128,6 +140,11 @@ template <>
 __device__ __forceinline__ float below_one<float>() {
     return 0x1.fffffep-1f;
 }
+
+// Crossing parameter (face - a) / d: IEEE division in FP64; in the FP32 kernel
+// the fast divide (its 2-ulp error is far below the FP32 state's own rounding).
+__device__ __forceinline__ double cross_t(double num, double d) { return num / d; }
+__device__ __forceinline__ float cross_t(float num, float d) { return __fdividef(num, d); }
 
 template <class R>
 __device__ __forceinline__ void sort3(R& a, R& b, R& c) {
@@ -187,7 +204,8 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
     const bool tail = lane == 31 || knext != key;
     const unsigned heads = __ballot_sync(FULL, head);
     const int start = 31 - __clz(heads & (FULL >> (31 - lane)));
-    const int longest = __reduce_max_sync(FULL, (unsigned)(lane - start + 1));
+    // only runs of real keys need summing (lanes with nothing to deposit form -1 runs)
+    const int longest = __reduce_max_sync(FULL, key >= 0 ? (unsigned)(lane - start + 1) : 0u);
     for (int dd = 1; dd < longest; dd <<= 1) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
@@ -253,15 +271,15 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     const int hx = sxb ? tx - 1 : tx, hy = syb ? ty - 1 : ty, hz = szb ? tz - 1 : tz;
     const R gxf = fx + (sxb ? hf : -hf), gyf = fy + (syb ? hf : -hf), gzf = fz + (szb ? hf : -hf);
     R Ex, Ey, Ez, Bx, By, Bz;
-    if constexpr (Tile<R, S>::kExpand) {
-        using V = typename Tile<R, S>::V;
-        const V* X = static_cast<const V*>(Fv);
-        Ex = tri_x<T>(X + 0 * T3, hx, ty, tz, gxf, fy, fz);
-        Ey = tri_x<T>(X + 1 * T3, tx, hy, tz, fx, gyf, fz);
-        Ez = tri_x<T>(X + 2 * T3, tx, ty, hz, fx, fy, gzf);
-        Bx = tri_x<T>(X + 3 * T3, tx, hy, hz, fx, gyf, gzf);
-        By = tri_x<T>(X + 4 * T3, hx, ty, hz, gxf, fy, gzf);
-        Bz = tri_x<T>(X + 5 * T3, hx, hy, tz, gxf, gyf, fz);
+    if constexpr (Tile<R, S>::kCoef) {
+        constexpr int NE = Tile<R, S>::NE;
+        const Coef<R>* X = static_cast<const Coef<R>*>(Fv);
+        Ex = tri_coef<R, T>(X + 0 * NE, hx, ty, tz, gxf, fy, fz);
+        Ey = tri_coef<R, T>(X + 1 * NE, tx, hy, tz, fx, gyf, fz);
+        Ez = tri_coef<R, T>(X + 2 * NE, tx, ty, hz, fx, fy, gzf);
+        Bx = tri_coef<R, T>(X + 3 * NE, tx, hy, hz, fx, gyf, gzf);
+        By = tri_coef<R, T>(X + 4 * NE, hx, ty, hz, gxf, fy, gzf);
+        Bz = tri_coef<R, T>(X + 5 * NE, hx, hy, tz, gxf, gyf, fz);
     } else {
         const R* F = static_cast<const R*>(Fv);
         Ex = tri_raw<R, T>(F + 0 * T3, hx, ty, tz, gxf, fy, fz);
@@ -316,15 +334,18 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
         // parameter t; piece s spans [t_s, t_{s+1}] and lies in the cell that
         // holds its midpoint
         R t1 = R(1), t2 = R(1), t3 = R(1);
-        if (sx) t1 = (R(sx > 0 ? 1 : 0) - fx) / dx;
-        if (sy) t2 = (R(sy > 0 ? 1 : 0) - fy) / dy;
-        if (sz) t3 = (R(sz > 0 ? 1 : 0) - fz) / dz;
+        if (sx) t1 = cross_t(R(sx > 0 ? 1 : 0) - fx, dx);
+        if (sy) t2 = cross_t(R(sy > 0 ? 1 : 0) - fy, dy);
+        if (sz) t3 = cross_t(R(sz > 0 ? 1 : 0) - fz, dz);
         sort3(t1, t2, t3);
+        // first piece [0, t1]: starts at the offset itself and stays in the start cell
+        deposit_segment<R, TJ>(Jt, dep ? (jz * TJ + jy) * TJ + jx : -1, fx, fy, fz, t1 * dx, t1 * dy, t1 * dz, Qx, Qy,
+                               Qz);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 1; s < 4; ++s) {
             if (!__any_sync(FULL, dep && s < nseg)) break;
-            const R ta = s == 0 ? R(0) : (s == 1 ? t1 : (s == 2 ? t2 : t3));
-            const R tb = s == 0 ? t1 : (s == 1 ? t2 : (s == 2 ? t3 : R(1)));
+            const R ta = s == 1 ? t1 : (s == 2 ? t2 : t3);
+            const R tb = s == 1 ? t2 : (s == 2 ? t3 : R(1));
             const bool on = dep && s < nseg && tb > ta;
             const R pax = fma(ta, dx, fx), pay = fma(ta, dy, fy), paz = fma(ta, dz, fz);
             const R dt = tb - ta;
@@ -374,14 +395,13 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
                                             double* __restrict__ J, double* __restrict__ ek_part,
                                             int* __restrict__ err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
-    constexpr bool kExpand = Tile<R, S>::kExpand;
-    using V = typename Tile<R, S>::V;
+    constexpr bool kCoef = Tile<R, S>::kCoef;
     extern __shared__ unsigned char smem_raw[];
-    // smem: raw TMA tile (re-used as the J tile once expanded) | vector tile
+    // smem: raw TMA tile (re-used as the J tile once the coefficients are built) | coefficient tile
     R* F = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    R* Jt = kExpand ? F : F + 6 * T3;
-    V* X = reinterpret_cast<V*>(F + 6 * T3);
-    const void* Fuse = kExpand ? static_cast<const void*>(X) : static_cast<const void*>(F);
+    R* Jt = kCoef ? F : F + 6 * T3;
+    Coef<R>* X = reinterpret_cast<Coef<R>*>(F + 6 * T3);
+    const void* Fuse = kCoef ? static_cast<const void*>(X) : static_cast<const void*>(F);
     __shared__ uint64_t bar;
     __shared__ double red[NT / 32];
     const GridDev& g = pp.g;
@@ -404,7 +424,7 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
             // field tile: cells c0-2 .. c0+S+1, i.e. padded index c0 .. c0+S+3
             tma_load_4d(F, &tmEB, c0x, c0y, c0z, 0, &bar);
         }
-        if (!kExpand)
+        if (!kCoef)
             for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);
         const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT);
         if (__syncthreads_or(!ok)) {
@@ -412,8 +432,8 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
             return;
         }
         phase ^= 1u;
-        if (kExpand) {
-            expand_tile<T, NT>(F, X);
+        if (kCoef) {
+            build_coef<R, T, NT>(F, X);
             __syncthreads();
             for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);  // J tile over the raw tile
             __syncthreads();
@@ -449,8 +469,7 @@ constexpr int PUSH_NT = 256;
 template <class R, int S>
 size_t push_smem_bytes() {
     constexpr int T = S + 4, TJ = S + 3;
-    if (Tile<R, S>::kExpand)
-        return 128 + sizeof(R) * 6 * T * T * T + sizeof(typename Tile<R, S>::V) * 6 * T * T * T;
+    if (Tile<R, S>::kCoef) return 128 + sizeof(R) * 6 * T * T * T + sizeof(Coef<R>) * 6 * Tile<R, S>::NE;
     return 128 + sizeof(R) * (6 * T * T * T + 3 * TJ * TJ * TJ);
 }
 
