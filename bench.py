@@ -165,10 +165,10 @@ def _workload_desc(wl, precision):
         ", 1% density perturbation" if wl.meta.get("perturb_eps") else "", precision))
 
 
-def time_gpu(torch, pic, wl, precision, steps, warmup, clocks=None, with_timing=True):
+def time_gpu(torch, pic, wl, precision, steps, warmup, clocks=None, with_timing=True, supercell=4):
     """Device-timed steps of one simulation; returns a result dict."""
     prec = pic.FP64 if precision == "fp64" else pic.MIXED
-    sim = pic.Simulation.from_workload(wl, precision=prec, supercell=4)
+    sim = pic.Simulation.from_workload(wl, precision=prec, supercell=supercell)
     st = sim.stream
     for _ in range(warmup):
         sim.step(1)
@@ -373,6 +373,20 @@ def run_gpu(args):
         r3["sim"].close()
     if not args.no_adjoint:
         out["adjoint"] = time_adjoint(torch, pic, W)
+    if not args.no_sweep:
+        # supercell edge S (the paper's Tables 5-6 study): particle-steps/s per S
+        sweep = {}
+        wl3s = locals().get("wl3")
+        for label, wls, prec, sizes in (("fp64 c2", wl, "fp64", (2, 4, 8)), ("fp64 r", W.config("r"), "fp64", (2, 4, 8)),
+                                        ("mixed c3", wl3s, "mixed", (4, 8))):
+            wlx = wls if wls is not None else W.config("c3")
+            row = {}
+            for S in sizes:
+                rs = time_gpu(torch, pic, wlx, prec, 20, 3, with_timing=False, supercell=S)
+                row["S=%d" % S] = rs["npart"] * 20 / (rs["ms"] / 1e3)
+                rs["sim"].close()
+            sweep[label] = row
+        out["supercell_sweep"] = sweep
     if not args.no_replica:
         wlr = W.config("r")
         rr = time_gpu(torch, pic, wlr, "fp64", args.steps, args.warmup, with_timing=False)
@@ -408,6 +422,7 @@ def main():
     ap.add_argument("--no-replica", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
