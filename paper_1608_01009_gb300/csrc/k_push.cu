@@ -384,9 +384,12 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
 
 // Resident CTAs per SM the register budget is cut for (FP32: 4 CTAs of 256
 // threads at 64 registers; the FP64 kernel needs ~100 registers, i.e. 2).
+#ifndef PICGB_PUSH_MINB_F32
+#define PICGB_PUSH_MINB_F32 4
+#endif
 template <class R>
 constexpr int push_min_blocks() {
-    return sizeof(R) == 4 ? 4 : 2;
+    return sizeof(R) == 4 ? PICGB_PUSH_MINB_F32 : 2;
 }
 
 template <class R, int S, int NT>
@@ -464,7 +467,10 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
 }
 
 // ------------------------------------------------------------------ launchers
-constexpr int PUSH_NT = 256;
+#ifndef PICGB_PUSH_NT
+#define PICGB_PUSH_NT 256
+#endif
+constexpr int PUSH_NT = PICGB_PUSH_NT;
 
 template <class R, int S>
 size_t push_smem_bytes() {

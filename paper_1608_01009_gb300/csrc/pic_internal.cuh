@@ -93,7 +93,10 @@ struct StepParams {
     double qdt2m, dtd[3], cq[3], mass;
 };
 
-constexpr int CHUNK = 4096;  // most particles of one supercell handled by one CTA pass
+#ifndef PICGB_CHUNK
+#define PICGB_CHUNK 4096
+#endif
+constexpr int CHUNK = PICGB_CHUNK;  // most particles of one supercell handled by one CTA pass
 
 __host__ __device__ inline int pack_cell(int ix, int iy, int iz) { return ix | (iy << 10) | (iz << 20); }
 __host__ __device__ inline int cell_x(int c) { return c & 1023; }
