@@ -28,17 +28,17 @@ namespace picgb {
 
 constexpr int TAPE_NT = 256;
 
-// Thread -> particle map of the per-particle kernels: lane l of warp-row r
-// takes particle l * rows + r.  Id order is usually cell order (a cell's
-// particles are consecutive), so this spreads the 32 lanes of a warp over 32
-// distant particles and keeps their atomics off the same grid nodes; the
-// differentiable state of a run this size sits in L2, so the scattered loads
-// are cheap.
+// Thread -> particle map of the per-particle kernels: inside each block's tile
+// of TAPE_NT consecutive particles, lane l of warp w takes particle
+// l * (TAPE_NT / 32) + w.  Id order is usually cell order (a cell's particles
+// are consecutive), so the 32 lanes of a warp fall in up to 32 different
+// cells and their atomics rarely hit the same grid nodes, while each block
+// still reads one contiguous tile (the other warps find it in L1).
 __device__ __forceinline__ long long lane_strided(long long n, bool& ok) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long rows = (n + 31) / 32;
-    const long long p = (t & 31) * rows + (t >> 5);
-    ok = (t >> 5) < rows && p < n;
+    constexpr int W = TAPE_NT / 32;
+    const int t = threadIdx.x;
+    const long long p = (long long)blockIdx.x * TAPE_NT + (t & 31) * W + (t >> 5);
+    ok = p < n;
     return p;
 }
 
@@ -644,7 +644,7 @@ __global__ void k_adj_fold_add(double* __restrict__ L, double* __restrict__ scat
 
 // ------------------------------------------------------------------ launchers
 static dim3 agrid(const GridDev& g) { return dim3((g.n[0] + AF_BX - 1) / AF_BX, (g.n[1] + AF_BY - 1) / AF_BY, g.n[2]); }
-static int pgrid(long long n) { return (int)((32 * ((n + 31) / 32) + TAPE_NT - 1) / TAPE_NT); }
+static int pgrid(long long n) { return (int)((n + TAPE_NT - 1) / TAPE_NT); }
 
 cudaError_t tape_step_launch(cudaStream_t st, const TapeDev& T, long long n, const StepParams& sp, const double* EB,
                              double* J) {

@@ -232,11 +232,73 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
     }
 }
 
+// Current of one piece with plain shared atomics (the deferred crossing moves
+// of different lanes belong to different particles, rarely to the same cell).
+template <class R, int TJ>
+__device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy, R Qz) {
+    constexpr int TJ2 = TJ * TJ, TJ3 = TJ * TJ * TJ;
+    const R h = R(0.5), tw = R(1.0 / 12.0);
+    const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
+    const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
+    {
+        const R q = Qx * dx, qc = q * (dy * dz * tw), qo = q * oy, qm = q * my;
+        R* J = Jt + b;
+        atomicAdd(J, fma(qo, oz, qc));
+        atomicAdd(J + TJ, fma(qm, oz, -qc));
+        atomicAdd(J + TJ2, fma(qo, mz, -qc));
+        atomicAdd(J + TJ + TJ2, fma(qm, mz, qc));
+    }
+    {
+        const R q = Qy * dy, qc = q * (dx * dz * tw), qo = q * ox, qm = q * mx;
+        R* J = Jt + TJ3 + b;
+        atomicAdd(J, fma(qo, oz, qc));
+        atomicAdd(J + 1, fma(qm, oz, -qc));
+        atomicAdd(J + TJ2, fma(qo, mz, -qc));
+        atomicAdd(J + 1 + TJ2, fma(qm, mz, qc));
+    }
+    {
+        const R q = Qz * dz, qc = q * (dx * dy * tw), qo = q * ox, qm = q * mx;
+        R* J = Jt + 2 * TJ3 + b;
+        atomicAdd(J, fma(qo, oy, qc));
+        atomicAdd(J + 1, fma(qm, oy, -qc));
+        atomicAdd(J + TJ, fma(qo, my, -qc));
+        atomicAdd(J + 1 + TJ, fma(qm, my, qc));
+    }
+}
+
+// Villasenor-Buneman split of a move that leaves its start cell (corner key
+// k0 in the J tile, start offset a, displacement d): cut at every face crossed
+// (at most one per axis), pieces in order of the crossing parameter, each
+// piece deposited in the cell that holds its midpoint.
+template <class R, int TJ>
+__device__ void split_direct(R* Jt, int k0, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy, R Qz) {
+    const R bx = ax + dx, by = ay + dy, bz = az + dz;
+    const int sx = cell_shift(bx), sy = cell_shift(by), sz = cell_shift(bz);
+    R t1 = sx ? cross_t(R(sx > 0 ? 1 : 0) - ax, dx) : R(1);
+    R t2 = sy ? cross_t(R(sy > 0 ? 1 : 0) - ay, dy) : R(1);
+    R t3 = sz ? cross_t(R(sz > 0 ? 1 : 0) - az, dz) : R(1);
+    sort3(t1, t2, t3);
+    const R ts[5] = {R(0), t1, t2, t3, R(1)};
+    const int jx = k0 % TJ, jy = (k0 / TJ) % TJ, jz = k0 / (TJ * TJ);
+    for (int s = 0; s < 4; ++s) {
+        const R ta = ts[s], tb = ts[s + 1];
+        if (!(tb > ta)) continue;
+        const R pax = fma(ta, dx, ax), pay = fma(ta, dy, ay), paz = fma(ta, dz, az);
+        const R dt = tb - ta;
+        const R ddx = dt * dx, ddy = dt * dy, ddz = dt * dz;
+        const int ox = cell_shift(fma(R(0.5), ddx, pax)), oy = cell_shift(fma(R(0.5), ddy, pay)),
+                  oz = cell_shift(fma(R(0.5), ddz, paz));
+        piece_direct<R, TJ>(Jt, ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox), pax - R(ox), pay - R(oy), paz - R(oz),
+                            ddx, ddy, ddz, Qx, Qy, Qz);
+    }
+}
+
 // One particle per lane; all 32 lanes of the warp call it (lanes without a
 // particle pass valid = false).  Returns w (gamma - 1) of the new state.
 template <class R, int S>
 __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const PStore<R>& ps, int p, bool valid,
-                                       const PushParams& pp, int c0x, int c0y, int c0z, int* err) {
+                                       const PushParams& pp, int c0x, int c0y, int c0z, int* err,
+                                       const XQueue<R>& xq, int qbase, int* s_qn) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
     const GridDev& g = pp.g;
     const int cp = valid ? ps.cell[p] : INACTIVE;
@@ -324,36 +386,61 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     const R wq = dep ? w : R(0);
     const R Qx = prm<R>(pp.cq[0], pp.cq_f[0]) * wq, Qy = prm<R>(pp.cq[1], pp.cq_f[1]) * wq,
             Qz = prm<R>(pp.cq[2], pp.cq_f[2]) * wq;
-    const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
-    const int nseg = 1 + (sx != 0) + (sy != 0) + (sz != 0);
-    if (!__any_sync(FULL, dep && nseg > 1)) {
-        // no lane leaves its cell: one segment each
-        deposit_segment<R, TJ>(Jt, dep ? (jz * TJ + jy) * TJ + jx : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+    const int key0 = ((lz + 1) * TJ + (ly + 1)) * TJ + (lx + 1);
+    if constexpr (sizeof(R) == 8) {
+        // FP64: a crossing lane would make its whole warp execute the split on the
+        // FP64 pipe, so crossing moves are queued and split after the chunk by full
+        // warps; moves that stay in their cell deposit one segment each, summed per
+        // cell run
+        const bool cross = dep && (sx | sy | sz) != 0;
+        deposit_segment<R, TJ>(Jt, dep && !cross ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+        const unsigned cm = __ballot_sync(FULL, cross);
+        if (cm) {
+            const int lane = threadIdx.x & 31, first = __ffs(cm) - 1;
+            int base = 0;
+            if (lane == first) base = atomicAdd(s_qn, __popc(cm));
+            base = __shfl_sync(FULL, base, first);
+            if (cross) {
+                const int q = qbase + base + __popc(cm & ((1u << lane) - 1u));
+                xq.key[q] = key0;
+                xq.a[0][q] = fx;
+                xq.a[1][q] = fy;
+                xq.a[2][q] = fz;
+                xq.d[0][q] = dx;
+                xq.d[1][q] = dy;
+                xq.d[2][q] = dz;
+                xq.w[q] = wq;
+            }
+        }
     } else {
-        // cut each move at the faces it crosses, pieces in order of the crossing
-        // parameter t; piece s spans [t_s, t_{s+1}] and lies in the cell that
-        // holds its midpoint
-        R t1 = R(1), t2 = R(1), t3 = R(1);
-        if (sx) t1 = cross_t(R(sx > 0 ? 1 : 0) - fx, dx);
-        if (sy) t2 = cross_t(R(sy > 0 ? 1 : 0) - fy, dy);
-        if (sz) t3 = cross_t(R(sz > 0 ? 1 : 0) - fz, dz);
-        sort3(t1, t2, t3);
-        // first piece [0, t1]: starts at the offset itself and stays in the start cell
-        deposit_segment<R, TJ>(Jt, dep ? (jz * TJ + jy) * TJ + jx : -1, fx, fy, fz, t1 * dx, t1 * dy, t1 * dz, Qx, Qy,
-                               Qz);
+        // FP32: the split runs in the warp (its arithmetic is cheap); each piece is
+        // summed per cell run like a whole move
+        const int nseg = 1 + (sx != 0) + (sy != 0) + (sz != 0);
+        if (!__any_sync(FULL, dep && nseg > 1)) {
+            deposit_segment<R, TJ>(Jt, dep ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+        } else {
+            R t1 = R(1), t2 = R(1), t3 = R(1);
+            if (sx) t1 = cross_t(R(sx > 0 ? 1 : 0) - fx, dx);
+            if (sy) t2 = cross_t(R(sy > 0 ? 1 : 0) - fy, dy);
+            if (sz) t3 = cross_t(R(sz > 0 ? 1 : 0) - fz, dz);
+            sort3(t1, t2, t3);
+            // first piece [0, t1]: starts at the offset itself and stays in the start cell
+            deposit_segment<R, TJ>(Jt, dep ? key0 : -1, fx, fy, fz, t1 * dx, t1 * dy, t1 * dz, Qx, Qy, Qz);
+            const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
 #pragma unroll
-        for (int s = 1; s < 4; ++s) {
-            if (!__any_sync(FULL, dep && s < nseg)) break;
-            const R ta = s == 1 ? t1 : (s == 2 ? t2 : t3);
-            const R tb = s == 1 ? t2 : (s == 2 ? t3 : R(1));
-            const bool on = dep && s < nseg && tb > ta;
-            const R pax = fma(ta, dx, fx), pay = fma(ta, dy, fy), paz = fma(ta, dz, fz);
-            const R dt = tb - ta;
-            const R ddx = dt * dx, ddy = dt * dy, ddz = dt * dz;
-            const int ox = cell_shift(fma(R(0.5), ddx, pax)), oy = cell_shift(fma(R(0.5), ddy, pay)),
-                      oz = cell_shift(fma(R(0.5), ddz, paz));
-            deposit_segment<R, TJ>(Jt, on ? ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox) : -1, pax - R(ox),
-                                   pay - R(oy), paz - R(oz), ddx, ddy, ddz, Qx, Qy, Qz);
+            for (int s = 1; s < 4; ++s) {
+                if (!__any_sync(FULL, dep && s < nseg)) break;
+                const R ta = s == 1 ? t1 : (s == 2 ? t2 : t3);
+                const R tb = s == 1 ? t2 : (s == 2 ? t3 : R(1));
+                const bool on = dep && s < nseg && tb > ta;
+                const R pax = fma(ta, dx, fx), pay = fma(ta, dy, fy), paz = fma(ta, dz, fz);
+                const R dt = tb - ta;
+                const R ddx = dt * dx, ddy = dt * dy, ddz = dt * dz;
+                const int ox = cell_shift(fma(R(0.5), ddx, pax)), oy = cell_shift(fma(R(0.5), ddy, pay)),
+                          oz = cell_shift(fma(R(0.5), ddz, paz));
+                deposit_segment<R, TJ>(Jt, on ? ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox) : -1, pax - R(ox),
+                                       pay - R(oy), paz - R(oz), ddx, ddy, ddz, Qx, Qy, Qz);
+            }
         }
     }
     if (!act) return R(0);
@@ -394,7 +481,7 @@ constexpr int push_min_blocks() {
 
 template <class R, int S, int NT>
 __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<R> ps,
-                                            const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
+                                            XQueue<R> xq, const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
                                             double* __restrict__ J, double* __restrict__ ek_part,
                                             int* __restrict__ err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
@@ -407,11 +494,14 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
     const void* Fuse = kCoef ? static_cast<const void*>(X) : static_cast<const void*>(F);
     __shared__ uint64_t bar;
     __shared__ double red[NT / 32];
+    __shared__ int s_qn;  // entries in this CTA's crossing queue
     const GridDev& g = pp.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int qbase = blockIdx.x * CHUNK;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
+        s_qn = 0;
     }
     __syncthreads();
     uint32_t phase = 0;
@@ -445,10 +535,21 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         R ek_chunk = R(0);  // at most CHUNK / NT particles per lane
         for (int base = ch.start + warp * 32; base < end; base += NT) {
             const int p = base + lane;
-            ek_chunk += push_lane<R, S>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err);
+            ek_chunk += push_lane<R, S>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err, xq, qbase, &s_qn);
         }
         ek += (double)ek_chunk;
         __syncthreads();
+        // the deferred crossing moves (FP64), split by every thread of the CTA
+        const int nq = sizeof(R) == 8 ? s_qn : 0;
+        for (int i = threadIdx.x; i < nq; i += NT) {
+            const int q = qbase + i;
+            const R w = xq.w[q];
+            split_direct<R, TJ>(Jt, xq.key[q], xq.a[0][q], xq.a[1][q], xq.a[2][q], xq.d[0][q], xq.d[1][q], xq.d[2][q],
+                                prm<R>(pp.cq[0], pp.cq_f[0]) * w, prm<R>(pp.cq[1], pp.cq_f[1]) * w,
+                                prm<R>(pp.cq[2], pp.cq_f[2]) * w);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_qn = 0;
         // merge: J tile cell t is domain cell c0 - 1 + t, padded index c0 + 1 + t
         for (int i = threadIdx.x; i < 3 * TJ3; i += NT) {
             const R v = Jt[i];
@@ -490,16 +591,18 @@ cudaError_t push_setup(int* blocks_per_sm) {
 
 template <class R, int S>
 cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
-                        const Chunk* chunks, const int* nchunks, double* J, double* ek_part, int* err) {
-    k_push<R, S, PUSH_NT><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, chunks, nchunks, J, ek_part,
-                                                                         err);
+                        const XQueue<R>& xq, const Chunk* chunks, const int* nchunks, double* J, double* ek_part,
+                        int* err) {
+    k_push<R, S, PUSH_NT><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, xq, chunks, nchunks, J,
+                                                                         ek_part, err);
     return cudaGetLastError();
 }
 
 #define PICGB_PUSH_INST(R, S)                                                                                   \
     template cudaError_t push_setup<R, S>(int*);                                                                \
     template cudaError_t push_launch<R, S>(int, cudaStream_t, const CUtensorMap&, const PushParams&,            \
-                                           const PStore<R>&, const Chunk*, const int*, double*, double*, int*); \
+                                           const PStore<R>&, const XQueue<R>&, const Chunk*, const int*, double*, \
+                                           double*, int*);                                                      \
     template size_t push_smem_bytes<R, S>();
 PICGB_PUSH_INST(double, 2)
 PICGB_PUSH_INST(double, 4)

@@ -128,6 +128,8 @@ struct pic_ctx {
     float* EB32 = nullptr;
     CUtensorMap tm64{}, tm32{};
     int push_grid = 0;
+    XQueue<double> xq64{};  // crossing-move queues of the particle kernel (push_grid x CHUNK entries)
+    XQueue<float> xq32{};
     std::vector<Species> sp;
     int* d_err = nullptr;
     int* d_keys = nullptr;
@@ -310,17 +312,40 @@ int sort_all(pic_ctx* c) {
 }
 
 template <class R>
+XQueue<R>& xqueue_of(pic_ctx* c);
+template <>
+XQueue<double>& xqueue_of<double>(pic_ctx* c) { return c->xq64; }
+template <>
+XQueue<float>& xqueue_of<float>(pic_ctx* c) { return c->xq32; }
+
+template <class R>
+int alloc_xqueue(pic_ctx* c) {
+    XQueue<R>& q = xqueue_of<R>(c);
+    const size_t n = (size_t)c->push_grid * CHUNK;
+    int r = dalloc(c, c->allocs, &q.key, n);
+    for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, c->allocs, &q.a[a], n);
+    for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, c->allocs, &q.d[a], n);
+    if (!r) r = dalloc(c, c->allocs, &q.w, n);
+    return r;
+}
+
+template <class R>
 int push_species(pic_ctx* c, Species& s) {
     PushParams pp = make_params(c, s);
+    const XQueue<R>& xq = xqueue_of<R>(c);
     const CUtensorMap& tm = c->mixed ? c->tm32 : c->tm64;
     cudaError_t e = cudaErrorInvalidValue;
     PStore<R>& ps = store_of<R>(s).a();
     const int S = c->g.S;
     if constexpr (sizeof(R) == 8) {
-        if (S == 2) e = push_launch<double, 2>(c->push_grid, c->st, tm, pp, ps, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+        if (S == 2)
+            e = push_launch<double, 2>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
+                                       c->d_err);
     }
-    if (S == 4) e = push_launch<R, 4>(c->push_grid, c->st, tm, pp, ps, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
-    if (S == 8) e = push_launch<R, 8>(c->push_grid, c->st, tm, pp, ps, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+    if (S == 4)
+        e = push_launch<R, 4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+    if (S == 8)
+        e = push_launch<R, 8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push launch: %s", cudaGetErrorString(e));
     c->launches += 1;
     return PIC_OK;
@@ -879,6 +904,7 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
         return bail(r);
     if (bps < 1) bps = 1;
     c->push_grid = c->nsm * bps;
+    if (!c->mixed && (r = alloc_xqueue<double>(c))) return bail(r);  // the FP32 kernel splits in the warp
     *out = c;
     return PIC_OK;
 }

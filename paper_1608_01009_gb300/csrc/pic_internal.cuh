@@ -74,6 +74,17 @@ struct PushParams {
     float qdt2m_f, dtd_f[3], cq_f[3];
 };
 
+// Per-CTA queue of the moves that leave their start cell (structure of arrays,
+// CHUNK entries per CTA starting at blockIdx.x * CHUNK): the particle kernel
+// defers their Villasenor-Buneman split to one dense pass per chunk.
+template <class R>
+struct XQueue {
+    int* key;   // J-tile corner index of the start cell
+    R* a[3];    // start offset in the cell
+    R* d[3];    // displacement (cells)
+    R* w;       // weight
+};
+
 // Differentiable path: id-ordered FP64 particle state, its cotangents, and the
 // per-species step constants.
 struct TapeDev {
@@ -201,6 +212,7 @@ template <class R, int S>
 cudaError_t push_setup(int* blocks_per_sm);
 template <class R, int S>
 cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
-                        const Chunk* chunks, const int* nchunks, double* J, double* ek_part, int* err);
+                        const XQueue<R>& xq, const Chunk* chunks, const int* nchunks, double* J, double* ek_part,
+                        int* err);
 
 }  // namespace picgb
