@@ -98,6 +98,22 @@ def test_adjoint_matches_oracle_tangent():
     assert abs(got - dwk_o) <= 1e-9 * abs(dwk_o), (got, dwk_o)
 
 
+def test_adjoint_matches_oracle_tangent_laser_ramp():
+    # x absorbing, Gaussian pulse, weight ramp (config-5 features at small size)
+    wl = W.laser_ramp(n=(32, 8, 8), ppc=2, a0=2.0, wavelength_cells=8, waist_cells=3.0, duration_wavelengths=2,
+                      ramp=(16, 24), seed=19)
+    nsteps = 40
+    wk, dE0, dB0, dP = _gpu_gradient(wl, nsteps, 9)
+    vE, vB, vx, vu = _directions(wl, seed=23)
+    ora = O.Oracle.from_workload(wl)
+    ptan = [[np.array(a, dtype=np.float64, copy=True) for a in (vx[0], vx[1], vx[2], vu[0], vu[1], vu[2])] +
+            [np.zeros(wl.species[0].n)]]
+    wk_o, dwk_o = ora.step_tangent(vE.copy(), vB.copy(), ptan, nsteps)
+    assert abs(wk - wk_o) <= 1e-12 * abs(wk_o)
+    got = _directional(dE0, dB0, dP, vE, vB, vx, vu)
+    assert abs(got - dwk_o) <= 1e-9 * abs(dwk_o), (got, dwk_o)
+
+
 def test_adjoint_matches_central_differences():
     wl = _small_slab()
     nsteps = 24

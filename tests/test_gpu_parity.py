@@ -196,3 +196,11 @@ def test_non_finite_input_is_reported_not_trapped():
         sim.energy()
     assert ei.value.code == -5  # PIC_ERR_NAN
     sim.close()
+
+
+def test_laser_ramp_small():
+    # config-5 features at small size: x absorbing, Gaussian transverse pulse,
+    # density ramp through the weights (weights from ~0 at the ramp foot)
+    wl = W.laser_ramp(n=(32, 16, 16), ppc=2, a0=3.0, wavelength_cells=8, waist_cells=4.0,
+                      duration_wavelengths=2, ramp=(16, 24), seed=17)
+    _check_one_step(wl, warm_steps=12)
