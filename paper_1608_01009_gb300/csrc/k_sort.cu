@@ -37,21 +37,49 @@ __device__ __forceinline__ int cell_key(const GridDev& g, int cp) {
     return (((sc << sh) + (iz & m)) << (2 * sh)) + ((iy & m) << sh) + (ix & m);
 }
 
+// U independent warp-aggregated slot claims: every lane's U match/atomic
+// chains are issued before the first result is needed, so U atomics per lane
+// are in flight at once (one atomic per distinct key per warp and group).
+template <int U>
+__device__ __forceinline__ void warp_agg_slots(int* counters, const int (&key)[U], int (&slot)[U]) {
+    const int lane = threadIdx.x & 31;
+    unsigned peers[U];
+    int leader[U], base[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+        peers[i] = __match_any_sync(0xffffffffu, key[i]);
+        leader[i] = __ffs(peers[i]) - 1;
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i)
+        base[i] = (lane == leader[i] && key[i] >= 0) ? atomicAdd(&counters[key[i]], __popc(peers[i])) : 0;
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+        const int b = __shfl_sync(0xffffffffu, base[i], leader[i]);
+        slot[i] = key[i] >= 0 ? b + __popc(peers[i] & ((1u << lane) - 1u)) : -1;
+    }
+}
+
+// Lane-interleaved groups of U x 32 particles per warp and iteration.
+constexpr int COUNT_U = 4;
+
 template <class R>
 __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long long* __restrict__ n_cur, GridDev g,
                                                        int* __restrict__ keys, int* __restrict__ counts) {
     const long long N = *n_cur;
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * SORT_NT;
-    for (long long base = (long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31); base < N; base += stride) {
-        const long long p = base + lane;
-        int key = -1;
-        if (p < N) {
-            const int cp = ps.cell[p];
-            key = cp < 0 ? -1 : cell_key(g, cp);
-            keys[p] = key;
+    const long long stride = (long long)gridDim.x * SORT_NT * COUNT_U;
+    for (long long base = ((long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31)) * COUNT_U; base < N;
+         base += stride) {
+        int key[COUNT_U], slot[COUNT_U];
+#pragma unroll
+        for (int i = 0; i < COUNT_U; ++i) {
+            const long long p = base + i * 32 + lane;
+            const int cp = p < N ? ps.cell[p] : INACTIVE;
+            key[i] = cp < 0 ? -1 : cell_key(g, cp);
+            if (p < N) keys[p] = key[i];
         }
-        warp_agg_slot(counts, key);
+        warp_agg_slots<COUNT_U>(counts, key, slot);
     }
 }
 
@@ -176,24 +204,54 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_add(int* __restrict__ counts, 
     }
 }
 
+// FP32 records (36 B) four per lane, FP64 (64 B) two: about 150 B in flight
+// per lane.  Each lane loads its whole records before claiming their slots,
+// so the loads overlap the slot atomics.
+template <class R>
+struct ScatterU {
+    static constexpr int U = sizeof(R) == 8 ? 2 : 4;
+};
+
 template <class R>
 __global__ void __launch_bounds__(SORT_NT) k_sort_scatter(PStore<R> src, PStore<R> dst, const long long* __restrict__ n_cur,
                                                          const int* __restrict__ keys, int* __restrict__ cursor) {
+    constexpr int U = ScatterU<R>::U;
     const long long N = *n_cur;
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * SORT_NT;
-    for (long long base = (long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31); base < N; base += stride) {
-        const long long p = base + lane;
-        const int key = p < N ? keys[p] : -1;
-        const int q = warp_agg_slot(cursor, key);
-        if (q >= 0) {
-            dst.cell[q] = src.cell[p];
-            for (int a = 0; a < 3; ++a) {
-                dst.off[a][q] = src.off[a][p];
-                dst.u[a][q] = src.u[a][p];
+    const long long stride = (long long)gridDim.x * SORT_NT * U;
+    for (long long base = ((long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31)) * U; base < N; base += stride) {
+        int key[U], slot[U], cell[U], id[U];
+        R off[U][3], u[U][3], w[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long p = base + i * 32 + lane;
+            key[i] = -1;
+            if (p < N) {
+                key[i] = keys[p];
+                cell[i] = src.cell[p];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    off[i][a] = src.off[a][p];
+                    u[i][a] = src.u[a][p];
+                }
+                w[i] = src.w[p];
+                id[i] = src.id[p];
             }
-            dst.w[q] = src.w[p];
-            dst.id[q] = src.id[p];
+        }
+        warp_agg_slots<U>(cursor, key, slot);
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int q = slot[i];
+            if (q >= 0) {
+                dst.cell[q] = cell[i];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    dst.off[a][q] = off[i][a];
+                    dst.u[a][q] = u[i][a];
+                }
+                dst.w[q] = w[i];
+                dst.id[q] = id[i];
+            }
         }
     }
 }
