@@ -355,6 +355,24 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """One reduced case (inputs still larger than L2, 2 GB of particle store)
+    for profiler captures; prints its device-timed rate, not a bench line."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1608_01009_gb300 import pic, workloads as W
+    if args.profile_case == "fp64":
+        wl, prec = W.config("c2"), "fp64"
+    else:
+        wl, prec = W.uniform_plasma((96, 96, 96), 32, 0.05, 0.1, seed=1241, steps=args.steps, name="mixed-96"), "mixed"
+    r = time_gpu(torch, pic, wl, prec, args.steps, args.warmup)
+    print(json.dumps({"profile_case": args.profile_case, "workload": _workload_desc(wl, prec),
+                      "particle_steps_per_s": r["npart"] * args.steps / (r["ms"] / 1e3),
+                      "stage_ms_per_step": {k: round(v, 4) for k, v in r["stage_ms"].items()}}))
+    r["sim"].close()
+    return 0
+
+
 def run_gpu(args):
     ws, rank, local = _dist()
     import torch
@@ -471,6 +489,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--laser-ramp", action="store_true",
                     help="run the 134 M-particle laser-plasma workload with its 50-step adjoint instead")
+    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
+                    help="run only one reduced case for ncu captures (a few GB on the device): "
+                         "fp64 = the 64^3 x 50 FP64 plasma, mixed = a 96^3 x 32 mixed plasma")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -478,6 +499,8 @@ def main():
         return run_reference(args)
     if args.laser_ramp:
         return run_laser_ramp(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_gpu(args)
 
 

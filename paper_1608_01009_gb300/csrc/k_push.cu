@@ -161,13 +161,86 @@ __device__ __forceinline__ void sort3(R& a, R& b, R& c) {
     b = hi;
 }
 
+// Sum of c[0..11] over the 32 lanes, reduced and scattered by recursive
+// halving: five butterfly rounds (partners lane ^ 16, 8, 4, 2, 1) that halve
+// the values each lane carries, 13 adds and 13 shuffles per lane instead of
+// 12 per round of a full scan.  Lane L ends with the total of value index
+// reduce12_index(L); reduce12_owner(L) marks one lane per index.
+template <class R>
+__device__ __forceinline__ R reduce_scatter12(const R (&c)[12]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    R x[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = (b4 ? c[i + 6] : c[i]) + __shfl_xor_sync(FULL, b4 ? c[i] : c[i + 6], 16);
+    R y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = (b3 ? x[i + 3] : x[i]) + __shfl_xor_sync(FULL, b3 ? x[i] : x[i + 3], 8);
+    // three values over a pair: lanes without bit 2 keep two, lanes with it one
+    const R z0 = (b2 ? y[2] : y[0]) + __shfl_xor_sync(FULL, b2 ? y[0] : y[2], 4);
+    const R z1 = y[1] + __shfl_xor_sync(FULL, y[1], 4);
+    const R keep = (!b2 && b1) ? z1 : z0;
+    const R w = keep + __shfl_xor_sync(FULL, (!b2 && !b1) ? z1 : z0, 2);
+    return w + __shfl_xor_sync(FULL, w, 1);
+}
+__device__ __forceinline__ int reduce12_index(int lane) {
+    return 6 * ((lane >> 4) & 1) + 3 * ((lane >> 3) & 1) + ((lane & 4) ? 2 : ((lane >> 1) & 1));
+}
+__device__ __forceinline__ bool reduce12_owner(int lane) { return (lane & 4) ? (lane & 3) == 0 : (lane & 1) == 0; }
+
+// The 12 edge values of one cell, v[0..11] = Jx (i+1/2, j+s1, k+s2), Jy
+// (i+s1, j+1/2, k+s2), Jz (i+s1, j+s2, k+1/2) with (s1, s2) = (0,0), (1,0),
+// (0,1), (1,1): offset of value m from the cell's corner in the J tile.
+template <int TJ>
+__device__ __forceinline__ int edge_offset(int m) {
+    const int comp = m >> 2, e = m & 3;
+    return comp * TJ * TJ * TJ + (e & 1) * (comp == 0 ? TJ : 1) + (e >> 1) * (comp == 2 ? TJ : TJ * TJ);
+}
+
+// Per distinct key of the warp: the lanes holding it contribute their v, the
+// rest zeros, one reduce-scatter, 12 owner lanes add the totals to the tile.
+template <class R, int TJ>
+__device__ __forceinline__ void deposit_by_key(R* Jt, int key, const R (&v)[12]) {
+    const int lane = threadIdx.x & 31;
+    const int eo = edge_offset<TJ>(reduce12_index(lane));
+    const bool owner = reduce12_owner(lane);
+    unsigned todo = __ballot_sync(FULL, key >= 0);
+    while (todo) {
+        const int k = __shfl_sync(FULL, key, __ffs(todo) - 1);
+        const bool mine = key == k;
+        todo &= ~__ballot_sync(FULL, mine);
+        R c[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) c[i] = mine ? v[i] : R(0);
+        const R t = reduce_scatter12<R>(c);
+        if (owner) atomicAdd(Jt + k + eo, t);
+    }
+}
+
+// Which warp reduction is cheaper for the FP64 pipe: one reduce-scatter per
+// distinct key (at most nruns of them, 13 adds each) or a segmented scan of
+// `rounds` rounds (12 adds each).  The FP32 kernel is bound by instruction
+// issue, not by its adds, and the per-key path issues more instructions
+// (selects, ballots, shuffles): it keeps the scan.
+#ifndef PICGB_KEYRED
+#define PICGB_KEYRED 1  // 0: segmented scan only
+#endif
+template <class R>
+struct DepositCost {
+    __device__ static bool channels_win(int nruns, int rounds) {
+        if constexpr (PICGB_KEYRED == 0 || sizeof(R) == 4) return false;
+        else return nruns * 13 <= rounds * 12;
+    }
+};
+
 // Current of one straight segment per lane, inside the cell whose J-tile
 // corner index is `key` (-1: nothing to deposit): start a (cell-relative) and
 // displacement d, in cells.  The 12 edge values are the line integrals of the
 // two transverse CIC weights, Q d_c [W(s1) W(s2) + sigma d_p d_r / 12]
-// (Villasenor-Buneman).  Lanes are ordered by cell, so runs of lanes with the
-// same key are first summed by a segmented warp scan; the last lane of each
-// run adds the run's 12 totals to the shared J tile.
+// (Villasenor-Buneman).  Lanes are ordered by cell, so lanes with the same
+// key are summed in the warp before the shared-memory atomics: by one
+// reduce-scatter per distinct key when the warp holds few keys, else by a
+// segmented scan whose last lane per run adds the run's 12 totals.
 template <class R, int TJ>
 __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy,
                                                 R Qz) {
@@ -175,23 +248,24 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
     const R h = R(0.5), tw = R(1.0 / 12.0);
     const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
     const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
+    const R vol = dx * dy * (dz * tw);  // sigma term d_x d_y d_z / 12, shared by the 3 components
     R v[12];
     {  // Jx on edges (i+1/2, j+s1, k+s2)
-        const R q = Qx * dx, qc = q * (dy * dz * tw), qo = q * oy, qm = q * my;
+        const R q = Qx * dx, qc = Qx * vol, qo = q * oy, qm = q * my;
         v[0] = fma(qo, oz, qc);
         v[1] = fma(qm, oz, -qc);
         v[2] = fma(qo, mz, -qc);
         v[3] = fma(qm, mz, qc);
     }
     {  // Jy on edges (i+s1, j+1/2, k+s2)
-        const R q = Qy * dy, qc = q * (dx * dz * tw), qo = q * ox, qm = q * mx;
+        const R q = Qy * dy, qc = Qy * vol, qo = q * ox, qm = q * mx;
         v[4] = fma(qo, oz, qc);
         v[5] = fma(qm, oz, -qc);
         v[6] = fma(qo, mz, -qc);
         v[7] = fma(qm, mz, qc);
     }
     {  // Jz on edges (i+s1, j+s2, k+1/2)
-        const R q = Qz * dz, qc = q * (dx * dy * tw), qo = q * ox, qm = q * mx;
+        const R q = Qz * dz, qc = Qz * vol, qo = q * ox, qm = q * mx;
         v[8] = fma(qo, oy, qc);
         v[9] = fma(qm, oy, -qc);
         v[10] = fma(qo, my, -qc);
@@ -206,6 +280,12 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
     const int start = 31 - __clz(heads & (FULL >> (31 - lane)));
     // only runs of real keys need summing (lanes with nothing to deposit form -1 runs)
     const int longest = __reduce_max_sync(FULL, key >= 0 ? (unsigned)(lane - start + 1) : 0u);
+    const int nruns = __popc(__ballot_sync(FULL, head && key >= 0));
+    const int rounds = longest > 1 ? 32 - __clz(longest - 1) : 0;
+    if (DepositCost<R>::channels_win(nruns, rounds)) {
+        deposit_by_key<R, TJ>(Jt, key, v);
+        return;
+    }
     for (int dd = 1; dd < longest; dd <<= 1) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
@@ -240,8 +320,9 @@ __device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R d
     const R h = R(0.5), tw = R(1.0 / 12.0);
     const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
     const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
+    const R vol = dx * dy * (dz * tw);  // sigma term d_x d_y d_z / 12, shared by the 3 components
     {
-        const R q = Qx * dx, qc = q * (dy * dz * tw), qo = q * oy, qm = q * my;
+        const R q = Qx * dx, qc = Qx * vol, qo = q * oy, qm = q * my;
         R* J = Jt + b;
         atomicAdd(J, fma(qo, oz, qc));
         atomicAdd(J + TJ, fma(qm, oz, -qc));
@@ -249,7 +330,7 @@ __device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R d
         atomicAdd(J + TJ + TJ2, fma(qm, mz, qc));
     }
     {
-        const R q = Qy * dy, qc = q * (dx * dz * tw), qo = q * ox, qm = q * mx;
+        const R q = Qy * dy, qc = Qy * vol, qo = q * ox, qm = q * mx;
         R* J = Jt + TJ3 + b;
         atomicAdd(J, fma(qo, oz, qc));
         atomicAdd(J + 1, fma(qm, oz, -qc));
@@ -257,7 +338,7 @@ __device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R d
         atomicAdd(J + 1 + TJ2, fma(qm, mz, qc));
     }
     {
-        const R q = Qz * dz, qc = q * (dx * dy * tw), qo = q * ox, qm = q * mx;
+        const R q = Qz * dz, qc = Qz * vol, qo = q * ox, qm = q * mx;
         R* J = Jt + 2 * TJ3 + b;
         atomicAdd(J, fma(qo, oy, qc));
         atomicAdd(J + 1, fma(qm, oy, -qc));
@@ -357,7 +438,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     const R umx = fma(h, Ex, ux), umy = fma(h, Ey, uy), umz = fma(h, Ez, uz);
     const R hg = h * rsqrt(fma(umx, umx, fma(umy, umy, fma(umz, umz, R(1)))));
     const R tbx = hg * Bx, tby = hg * By, tbz = hg * Bz;
-    const R sf = R(2) / (R(1) + fma(tbx, tbx, fma(tby, tby, tbz * tbz)));
+    const R sf = R(2) / fma(tbx, tbx, fma(tby, tby, fma(tbz, tbz, R(1))));
     const R sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
     const R upx = fma(umy, tbz, fma(-umz, tby, umx));
     const R upy = fma(umz, tbx, fma(-umx, tbz, umy));
