@@ -109,10 +109,15 @@ typedef struct {
     void* stream;
 } pic_grid_desc;
 
-/* Species: charge q and mass m in units of e and m_e (electrons: -1, 1). */
+/* Species: charge q and mass m in units of e and m_e (electrons: -1, 1).
+ * immobile != 0 declares a neutralising background of immobile ions (the
+ * paper describes no ion model; this is the usual PIC convention): its
+ * particles are neither stored nor pushed and carry no current; the species
+ * keeps its id and reports 0 particles. */
 typedef struct {
     double q;
     double m;
+    int32_t immobile;
 } pic_species_desc;
 
 typedef struct pic_ctx pic_ctx;
@@ -149,6 +154,12 @@ PIC_API int pic_set_particles(pic_ctx* ctx, int species, int64_t n, const double
 PIC_API int pic_set_particles_dev(pic_ctx* ctx, int species, int64_t n, const double* x, const double* y,
                           const double* z, const double* ux, const double* uy, const double* uz,
                           const double* w);
+
+/* Species properties: q, m, the immobile flag, and nid, the number of ids
+ * given at the species' last load (ids run 0..nid-1; particles that left
+ * through an absorbing boundary keep their ids unused).  Any output pointer
+ * may be NULL. */
+PIC_API int pic_species_info(pic_ctx* ctx, int species, double* q, double* m, int32_t* immobile, int64_t* nid);
 
 /* Number of active particles of a species (synchronises the stream). */
 PIC_API int pic_count_particles(pic_ctx* ctx, int species, int64_t* n);
@@ -227,6 +238,23 @@ PIC_API int pic_tape_forward(pic_ctx* ctx, int nsteps, int ckpt_every, double* w
 PIC_API int pic_tape_backward(pic_ctx* ctx, double wk_weight, const double* const gE[3], const double* const gB[3],
                               double* const dE0[3], double* const dB0[3]);
 PIC_API int pic_tape_particle_grad(pic_ctx* ctx, int species, double* const dP[6]);
+
+/* Checkpoint and resume (the paper describes none; a library facility).
+ * pic_get_state with blob == NULL stores in *bytes the size of the context's
+ * state; with a host buffer of *bytes bytes it copies the whole state into
+ * it and synchronises: a header (grid descriptor, step counters, species
+ * count), the ghost-padded E, B, J grids, the last folded current, and every
+ * species' q, m and binned particle store in its internal precision and
+ * order, with its bin table.  PIC_ERR_ARG if *bytes is too small.
+ * pic_set_state restores a blob written by pic_get_state into a context
+ * created with the same descriptor (n, d, dt, bc, absorbing layer,
+ * precision, supercell, sort_interval; PIC_ERR_ARG otherwise), replacing all
+ * of its species and dropping a recorded tape; stepping on reproduces the
+ * saved run up to the summation order of floating-point atomics.  The blob
+ * is a plain byte image for this library build and machine (native byte
+ * order); the caller owns it. */
+PIC_API int pic_get_state(pic_ctx* ctx, void* blob, int64_t* bytes);
+PIC_API int pic_set_state(pic_ctx* ctx, const void* blob, int64_t bytes);
 
 /* Field energy W_F = 1/2 dx dy dz sum (E^2 + B^2) of caller-provided fields,
  * allocating nothing.  The paper has no counterpart: this is a library

@@ -374,12 +374,43 @@ __device__ void split_direct(R* Jt, int k0, R ax, R ay, R az, R dx, R dy, R dz, 
     }
 }
 
+// FP32 kernel with a coefficient tile: each warp keeps the moves that leave
+// their start cell in a small shared-memory queue (WQ entries of key, start
+// offset, displacement and weight, SoA) carved from the raw tile's space
+// behind the J tile, and splits them with all lanes once the queue is full
+// and at the end of the chunk.  A warp whose lanes cross in bulk splits them
+// at once.
+#ifndef PICGB_F32_QUEUE
+#define PICGB_F32_QUEUE 1
+#endif
+constexpr int WQ = 31;
+template <class R, int S, int NT>
+struct WarpQueue {
+    static constexpr int TJ = S + 3, T = S + 4;
+    static constexpr int OFF = (3 * TJ * TJ * TJ + 7) & ~7;  // floats behind the J tile
+    static constexpr bool kOn = PICGB_F32_QUEUE && sizeof(R) == 4 && Tile<R, S>::kCoef &&
+                                OFF + (NT / 32) * 8 * WQ <= 6 * T * T * T;
+};
+
+template <class R, int TJ>
+__device__ __forceinline__ void warp_queue_flush(R* Jt, const R* q, int n, const PushParams& pp) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const R w = q[7 * WQ + lane];
+        split_direct<R, TJ>(Jt, __float_as_int(q[lane]), q[WQ + lane], q[2 * WQ + lane], q[3 * WQ + lane],
+                            q[4 * WQ + lane], q[5 * WQ + lane], q[6 * WQ + lane], pp.cq_f[0] * w, pp.cq_f[1] * w,
+                            pp.cq_f[2] * w);
+    }
+    __syncwarp();
+}
+
 // One particle per lane; all 32 lanes of the warp call it (lanes without a
 // particle pass valid = false).  Returns w (gamma - 1) of the new state.
-template <class R, int S>
+template <class R, int S, int NT>
 __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const PStore<R>& ps, int p, bool valid,
                                        const PushParams& pp, int c0x, int c0y, int c0z, int* err,
-                                       const XQueue<R>& xq, int qbase, int* s_qn) {
+                                       const XQueue<R>& xq, int qbase, int* s_qn, R* wqueue, int& wq_n) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
     const GridDev& g = pp.g;
     const int cp = valid ? ps.cell[p] : INACTIVE;
@@ -493,6 +524,33 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
                 xq.w[q] = wq;
             }
         }
+    } else if constexpr (WarpQueue<R, S, NT>::kOn) {
+        const bool cross = dep && (sx | sy | sz) != 0;
+        deposit_segment<R, TJ>(Jt, dep && !cross ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+        const unsigned cm = __ballot_sync(FULL, cross);
+        if (cm) {
+            const int cnt = __popc(cm), lane = threadIdx.x & 31;
+            if (cnt >= 16) {
+                if (cross) split_direct<R, TJ>(Jt, key0, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+            } else {
+                if (wq_n + cnt > WQ) {
+                    warp_queue_flush<R, TJ>(Jt, wqueue, wq_n, pp);
+                    wq_n = 0;
+                }
+                if (cross) {
+                    const int q = wq_n + __popc(cm & ((1u << lane) - 1u));
+                    wqueue[q] = __int_as_float(key0);
+                    wqueue[WQ + q] = fx;
+                    wqueue[2 * WQ + q] = fy;
+                    wqueue[3 * WQ + q] = fz;
+                    wqueue[4 * WQ + q] = dx;
+                    wqueue[5 * WQ + q] = dy;
+                    wqueue[6 * WQ + q] = dz;
+                    wqueue[7 * WQ + q] = wq;
+                }
+                wq_n += cnt;
+            }
+        }
     } else {
         // FP32: the split runs in the warp (its arithmetic is cheap); each piece is
         // summed per cell run like a whole move
@@ -579,6 +637,8 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
     const GridDev& g = pp.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int qbase = blockIdx.x * CHUNK;
+    R* wqueue = F + WarpQueue<R, S, NT>::OFF + warp * 8 * WQ;  // used only where WarpQueue<..>::kOn
+    int wq_n = 0;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -616,7 +676,12 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         R ek_chunk = R(0);  // at most CHUNK / NT particles per lane
         for (int base = ch.start + warp * 32; base < end; base += NT) {
             const int p = base + lane;
-            ek_chunk += push_lane<R, S>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err, xq, qbase, &s_qn);
+            ek_chunk += push_lane<R, S, NT>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err, xq, qbase, &s_qn,
+                                            wqueue, wq_n);
+        }
+        if constexpr (WarpQueue<R, S, NT>::kOn) {
+            if (wq_n > 0) warp_queue_flush<R, TJ>(Jt, wqueue, wq_n, pp);
+            wq_n = 0;
         }
         ek += (double)ek_chunk;
         __syncthreads();

@@ -62,6 +62,7 @@ struct Store {
 
 struct Species {
     double q = 0, m = 1;
+    bool immobile = false;         // neutralising background: no particles stored
     long long cap = 0;
     Store<double> s64;
     Store<float> s32;
@@ -304,6 +305,7 @@ int sort_species(pic_ctx* c, Species& s) {
 
 int sort_all(pic_ctx* c) {
     for (auto& s : c->sp) {
+        if (s.immobile) continue;  // empty store, never pushed
         int r = c->mixed ? sort_species<float>(c, s) : sort_species<double>(c, s);
         if (r) return r;
     }
@@ -386,26 +388,39 @@ int ensure_keys(pic_ctx* c, long long n) {
     return PIC_OK;
 }
 
+// (Re)allocate the store and bin tables of species s for n particles.
+int alloc_species(pic_ctx* c, Species& s, long long n) {
+    cudaStreamSynchronize(c->st);
+    free_species(s);
+    long long cap = n > 0 ? n : 1;
+    s.cap = cap;
+    int r = dalloc(c, s.allocs, &s.d_n, 2);
+    if (!r) r = dalloc(c, s.allocs, &s.d_bin_start, (size_t)c->g.nbins + 1);
+    if (!r) r = dalloc(c, s.allocs, &s.d_chunks, (size_t)(c->g.nbins + cap / CHUNK + 1));
+    if (!r) r = dalloc(c, s.allocs, &s.d_nchunks, 1);
+    if (!r) r = c->mixed ? alloc_store(c, s, s.s32, cap) : alloc_store(c, s, s.s64, cap);
+    if (r) return r;
+    CUDA_TRY(c, cudaMemsetAsync(s.d_nchunks, 0, sizeof(int), c->st));
+    return PIC_OK;
+}
+
+// Sort keys for the largest species.
+int ensure_keys_all(pic_ctx* c) {
+    long long kmax = 1;
+    for (auto& o : c->sp) kmax = o.cap > kmax ? o.cap : kmax;
+    return ensure_keys(c, kmax);
+}
+
 // (Re)load the particles of species s from FP64 arrays (host or device).
 int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src, bool device) {
     if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", n);
     for (int k = 0; k < 7 && n > 0; ++k)
         if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array %d", k);
     if (!s.d_n || n > s.cap) {
-        cudaStreamSynchronize(c->st);
-        free_species(s);
-        long long cap = n > 0 ? n : 1;
-        s.cap = cap;
-        int r = dalloc(c, s.allocs, &s.d_n, 2);
-        if (!r) r = dalloc(c, s.allocs, &s.d_bin_start, (size_t)c->g.nbins + 1);
-        if (!r) r = dalloc(c, s.allocs, &s.d_chunks, (size_t)(c->g.nbins + cap / CHUNK + 1));
-        if (!r) r = dalloc(c, s.allocs, &s.d_nchunks, 1);
-        if (!r) r = c->mixed ? alloc_store(c, s, s.s32, cap) : alloc_store(c, s, s.s64, cap);
+        int r = alloc_species(c, s, n);
         if (r) return r;
     }
-    long long kmax = 0;
-    for (auto& o : c->sp) kmax = o.cap > kmax ? o.cap : kmax;
-    int r = ensure_keys(c, kmax > s.cap ? kmax : s.cap);
+    int r = ensure_keys_all(c);
     if (r) return r;
     // stage FP64 inputs on the device when they come from the host
     const double* dsrc[7];
@@ -433,6 +448,24 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
     return r;
 }
 
+// The kinetic-energy partials of all species, contiguous (push_grid slots
+// per species), zeroed.
+int rebuild_ek(pic_ctx* c) {
+    if (c->d_ekall) {
+        cudaStreamSynchronize(c->st);
+        cudaFree(c->d_ekall);
+        for (auto& p : c->allocs)
+            if (p == c->d_ekall) p = nullptr;
+        c->d_ekall = nullptr;
+    }
+    if (c->sp.empty()) return PIC_OK;
+    int r = dalloc(c, c->allocs, &c->d_ekall, (size_t)c->push_grid * c->sp.size());
+    if (r) return r;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_ekall, 0, sizeof(double) * c->push_grid * c->sp.size(), c->st));
+    for (size_t i = 0; i < c->sp.size(); ++i) c->sp[i].d_ek = c->d_ekall + i * c->push_grid;
+    return PIC_OK;
+}
+
 int add_species_impl(pic_ctx* c, const pic_species_desc* d, int64_t n, const double* const* src, bool device,
                      int* id) {
     if (!c) return PIC_ERR_ARG;
@@ -444,24 +477,19 @@ int add_species_impl(pic_ctx* c, const pic_species_desc* d, int64_t n, const dou
     Species& s = c->sp.back();
     s.q = d->q;
     s.m = d->m;
-    // kinetic partial slots for this species
-    int r = load_particles(c, s, n, src, device);
+    s.immobile = d->immobile != 0;
+    if (n < 0) {
+        c->sp.pop_back();
+        return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
+    }
+    // an immobile background keeps an empty store
+    int r = load_particles(c, s, s.immobile ? 0 : n, src, device);
     if (r) {
         free_species(s);
         c->sp.pop_back();
         return r;
     }
-    // rebuild the contiguous kinetic-partials buffer
-    if (c->d_ekall) {
-        cudaStreamSynchronize(c->st);
-        cudaFree(c->d_ekall);
-        for (auto& p : c->allocs)
-            if (p == c->d_ekall) p = nullptr;
-    }
-    r = dalloc(c, c->allocs, &c->d_ekall, (size_t)c->push_grid * c->sp.size());
-    if (r) return r;
-    CUDA_TRY(c, cudaMemsetAsync(c->d_ekall, 0, sizeof(double) * c->push_grid * c->sp.size(), c->st));
-    for (size_t i = 0; i < c->sp.size(); ++i) c->sp[i].d_ek = c->d_ekall + i * c->push_grid;
+    if ((r = rebuild_ek(c))) return r;
     *id = (int)c->sp.size() - 1;
     if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
     return PIC_OK;
@@ -826,6 +854,78 @@ int tape_backward_impl(pic_ctx* c, double wk_weight, const double* const gE[3], 
 }  // namespace
 
 // ====================================================================== ABI
+// ---------------------------------------------------------------- state blob
+namespace {
+
+const char STATE_MAGIC[8] = {'P', 'I', 'C', 'G', 'B', 'S', 'T', '1'};
+
+struct StateHeader {
+    char magic[8];
+    int32_t precision, supercell, sort_interval, absorb_cells;
+    int32_t n[3], bc[3];
+    int32_t nspecies, pad;
+    double d[3], dt, absorb_sigma;
+    int64_t steps, since_sort;
+};
+
+struct SpeciesHeader {
+    double q, m;
+    int64_t n, nid;
+    int32_t immobile, nchunks;
+};
+
+size_t pad8(size_t x) { return (x + 7) & ~size_t(7); }
+
+// Store and bin-table bytes of one species with n particles and nch chunks.
+size_t species_payload(const pic_ctx* c, long long n, int nch) {
+    const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+    return pad8(n * sizeof(int)) * 2 + 7 * pad8(n * rs) + pad8(((size_t)c->g.nbins + 1) * sizeof(int)) +
+           pad8((size_t)nch * sizeof(Chunk));
+}
+
+size_t grid_payload(const pic_ctx* c) {
+    const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    return (size_t)(9 * c->g.P + 3 * ncell) * sizeof(double);
+}
+
+// Host-side cursor over the blob; every access is bounds-checked.
+struct Cursor {
+    unsigned char* p;
+    size_t left;
+    bool take(size_t n, unsigned char** at) {
+        if (n > left) return false;
+        *at = p;
+        p += pad8(n) <= left ? pad8(n) : n;
+        left -= pad8(n) <= left ? pad8(n) : left;
+        return true;
+    }
+};
+
+bool same_desc(const StateHeader& h, const pic_grid_desc& d) {
+    bool ok = h.precision == d.precision && h.supercell == d.supercell && h.sort_interval == d.sort_interval &&
+              h.absorb_cells == d.absorb_cells && h.dt == d.dt && h.absorb_sigma == d.absorb_sigma;
+    for (int a = 0; a < 3; ++a) ok = ok && h.n[a] == d.n[a] && h.bc[a] == d.bc[a] && h.d[a] == d.d[a];
+    return ok;
+}
+
+template <class R>
+int copy_store(pic_ctx* c, Species& s, long long n, Cursor& cur, bool to_blob) {
+    PStore<R>& ps = store_of<R>(s).a();
+    void* dev[9] = {ps.cell, ps.off[0], ps.off[1], ps.off[2], ps.u[0], ps.u[1], ps.u[2], ps.w, ps.id};
+    const size_t es[9] = {sizeof(int), sizeof(R), sizeof(R), sizeof(R), sizeof(R), sizeof(R), sizeof(R), sizeof(R),
+                          sizeof(int)};
+    for (int k = 0; k < 9; ++k) {
+        unsigned char* at;
+        if (!cur.take(n * es[k], &at)) return fail(c, PIC_ERR_ARG, "state blob too small");
+        if (n > 0)
+            CUDA_TRY(c, to_blob ? cudaMemcpyAsync(at, dev[k], n * es[k], cudaMemcpyDeviceToHost, c->st)
+                                : cudaMemcpyAsync(dev[k], at, n * es[k], cudaMemcpyHostToDevice, c->st));
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
@@ -946,7 +1046,8 @@ static int set_particles_impl(pic_ctx* c, int species, int64_t n, const double* 
     if (!c) return PIC_ERR_ARG;
     if (species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
     CUDA_TRY(c, cudaSetDevice(c->dev));
-    int r = load_particles(c, c->sp[species], n, src, device);
+    Species& s = c->sp[species];
+    int r = load_particles(c, s, s.immobile ? 0 : n, src, device);
     if (r) return r;
     if (!device) CUDA_TRY(c, cudaStreamSynchronize(c->st));
     return PIC_OK;
@@ -962,6 +1063,17 @@ int pic_set_particles_dev(pic_ctx* c, int species, int64_t n, const double* x, c
                           const double* ux, const double* uy, const double* uz, const double* w) {
     const double* src[7] = {x, y, z, ux, uy, uz, w};
     return set_particles_impl(c, species, n, src, true);
+}
+
+int pic_species_info(pic_ctx* c, int species, double* q, double* m, int32_t* immobile, int64_t* nid) {
+    if (!c) return PIC_ERR_ARG;
+    if (species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
+    const Species& s = c->sp[species];
+    if (q) *q = s.q;
+    if (m) *m = s.m;
+    if (immobile) *immobile = s.immobile ? 1 : 0;
+    if (nid) *nid = s.nid;
+    return PIC_OK;
 }
 
 int pic_count_particles(pic_ctx* c, int species, int64_t* n) {
@@ -1029,6 +1141,7 @@ int pic_step(pic_ctx* c, int nsteps) {
         }
         stage_begin(c, 0, &e0);
         for (auto& s : c->sp) {
+            if (s.immobile) continue;
             int r = c->mixed ? push_species<float>(c, s) : push_species<double>(c, s);
             if (r) return r;
         }
@@ -1118,6 +1231,156 @@ int pic_launch_count(pic_ctx* c, int64_t* n, int reset) {
     if (!n) return fail(c, PIC_ERR_ARG, "null output");
     *n = c->launches;
     if (reset) c->launches = 0;
+    return PIC_OK;
+}
+
+int pic_get_state(pic_ctx* c, void* blob, int64_t* bytes) {
+    if (!c) return PIC_ERR_ARG;
+    if (!bytes) return fail(c, PIC_ERR_ARG, "null size");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    std::vector<long long> n(c->sp.size());
+    std::vector<int> nch(c->sp.size());
+    size_t total = pad8(sizeof(StateHeader)) + grid_payload(c);
+    for (size_t i = 0; i < c->sp.size(); ++i) {
+        CUDA_TRY(c, cudaMemcpy(&n[i], c->sp[i].d_n, sizeof(long long), cudaMemcpyDeviceToHost));
+        CUDA_TRY(c, cudaMemcpy(&nch[i], c->sp[i].d_nchunks, sizeof(int), cudaMemcpyDeviceToHost));
+        total += pad8(sizeof(SpeciesHeader)) + species_payload(c, n[i], nch[i]);
+    }
+    if (!blob) {
+        *bytes = (int64_t)total;
+        return PIC_OK;
+    }
+    if (*bytes < (int64_t)total) return fail(c, PIC_ERR_ARG, "state blob of %lld bytes, %zu needed", (long long)*bytes, total);
+    Cursor cur{static_cast<unsigned char*>(blob), (size_t)*bytes};
+    unsigned char* at;
+    cur.take(sizeof(StateHeader), &at);
+    StateHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, STATE_MAGIC, 8);
+    h.precision = c->desc.precision;
+    h.supercell = c->desc.supercell;
+    h.sort_interval = c->desc.sort_interval;
+    h.absorb_cells = c->desc.absorb_cells;
+    for (int a = 0; a < 3; ++a) {
+        h.n[a] = c->desc.n[a];
+        h.bc[a] = c->desc.bc[a];
+        h.d[a] = c->desc.d[a];
+    }
+    h.dt = c->desc.dt;
+    h.absorb_sigma = c->desc.absorb_sigma;
+    h.nspecies = (int32_t)c->sp.size();
+    h.steps = c->steps;
+    h.since_sort = c->since_sort;
+    memcpy(at, &h, sizeof h);
+    const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    cur.take(6 * c->g.P * sizeof(double), &at);
+    CUDA_TRY(c, cudaMemcpyAsync(at, c->EB, 6 * c->g.P * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    cur.take(3 * c->g.P * sizeof(double), &at);
+    CUDA_TRY(c, cudaMemcpyAsync(at, c->J, 3 * c->g.P * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    cur.take(3 * ncell * sizeof(double), &at);
+    CUDA_TRY(c, cudaMemcpyAsync(at, c->Jlast, 3 * ncell * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    for (size_t i = 0; i < c->sp.size(); ++i) {
+        Species& s = c->sp[i];
+        SpeciesHeader sh{s.q, s.m, (int64_t)n[i], (int64_t)s.nid, s.immobile ? 1 : 0, nch[i]};
+        cur.take(sizeof sh, &at);
+        memcpy(at, &sh, sizeof sh);
+        int r = c->mixed ? copy_store<float>(c, s, n[i], cur, true) : copy_store<double>(c, s, n[i], cur, true);
+        if (r) return r;
+        cur.take(((size_t)c->g.nbins + 1) * sizeof(int), &at);
+        CUDA_TRY(c, cudaMemcpyAsync(at, s.d_bin_start, ((size_t)c->g.nbins + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->st));
+        if (nch[i] > 0) {
+            cur.take((size_t)nch[i] * sizeof(Chunk), &at);
+            CUDA_TRY(c, cudaMemcpyAsync(at, s.d_chunks, (size_t)nch[i] * sizeof(Chunk), cudaMemcpyDeviceToHost, c->st));
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    *bytes = (int64_t)total;
+    return PIC_OK;
+}
+
+int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
+    if (!c) return PIC_ERR_ARG;
+    if (!blob || bytes < (int64_t)sizeof(StateHeader)) return fail(c, PIC_ERR_ARG, "null or short state blob");
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    Cursor cur{const_cast<unsigned char*>(static_cast<const unsigned char*>(blob)), (size_t)bytes};
+    unsigned char* at;
+    cur.take(sizeof(StateHeader), &at);
+    StateHeader h;
+    memcpy(&h, at, sizeof h);
+    if (memcmp(h.magic, STATE_MAGIC, 8) != 0) return fail(c, PIC_ERR_ARG, "not a state blob of this library");
+    if (!same_desc(h, c->desc)) return fail(c, PIC_ERR_ARG, "state blob was written for another grid descriptor");
+    if (h.nspecies < 0 || h.nspecies > MAX_SPECIES) return fail(c, PIC_ERR_ARG, "bad species count in state blob");
+    if (cur.left < grid_payload(c)) return fail(c, PIC_ERR_ARG, "state blob too small");
+    // validate every species section before touching the context
+    {
+        Cursor probe = cur;
+        const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+        unsigned char* q;
+        probe.take(6 * c->g.P * sizeof(double), &q);
+        probe.take(3 * c->g.P * sizeof(double), &q);
+        probe.take(3 * ncell * sizeof(double), &q);
+        for (int i = 0; i < h.nspecies; ++i) {
+            SpeciesHeader sh;
+            if (!probe.take(sizeof sh, &q)) return fail(c, PIC_ERR_ARG, "state blob too small");
+            memcpy(&sh, q, sizeof sh);
+            const long long maxch = c->g.nbins + (sh.n > 0 ? sh.n : 1) / CHUNK + 1;
+            if (sh.n < 0 || sh.n >= (1LL << 31) - 1 || sh.nchunks < 0 || sh.nchunks > maxch || !(sh.m > 0))
+                return fail(c, PIC_ERR_ARG, "bad species record in state blob");
+            const size_t need = species_payload(c, sh.n, sh.nchunks);
+            if (probe.left < need) return fail(c, PIC_ERR_ARG, "state blob too small");
+            probe.p += need;
+            probe.left -= need;
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    for (auto& s : c->sp) free_species(s);
+    c->sp.clear();
+    c->tape.release();
+    const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    cur.take(6 * c->g.P * sizeof(double), &at);
+    CUDA_TRY(c, cudaMemcpyAsync(c->EB, at, 6 * c->g.P * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    cur.take(3 * c->g.P * sizeof(double), &at);
+    CUDA_TRY(c, cudaMemcpyAsync(c->J, at, 3 * c->g.P * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    cur.take(3 * ncell * sizeof(double), &at);
+    CUDA_TRY(c, cudaMemcpyAsync(c->Jlast, at, 3 * ncell * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(c, refresh_launch(c->st, c->EB, c->g, c->EB32));
+    c->launches += 1;
+    for (int i = 0; i < h.nspecies; ++i) {
+        SpeciesHeader sh;
+        cur.take(sizeof sh, &at);
+        memcpy(&sh, at, sizeof sh);
+        c->sp.emplace_back();
+        Species& s = c->sp.back();
+        s.q = sh.q;
+        s.m = sh.m;
+        s.immobile = sh.immobile != 0;
+        s.nid = sh.nid;
+        int r = alloc_species(c, s, sh.n);
+        if (!r) r = c->mixed ? copy_store<float>(c, s, sh.n, cur, false) : copy_store<double>(c, s, sh.n, cur, false);
+        if (r) return r;
+        const long long nn[2] = {sh.n, sh.n};
+        CUDA_TRY(c, cudaMemcpyAsync(s.d_n, nn, sizeof nn, cudaMemcpyHostToDevice, c->st));
+        cur.take(((size_t)c->g.nbins + 1) * sizeof(int), &at);
+        CUDA_TRY(c, cudaMemcpyAsync(s.d_bin_start, at, ((size_t)c->g.nbins + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                                    c->st));
+        if (sh.nchunks > 0) {
+            cur.take((size_t)sh.nchunks * sizeof(Chunk), &at);
+            CUDA_TRY(c, cudaMemcpyAsync(s.d_chunks, at, (size_t)sh.nchunks * sizeof(Chunk), cudaMemcpyHostToDevice,
+                                        c->st));
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(s.d_nchunks, &sh.nchunks, sizeof(int), cudaMemcpyHostToDevice, c->st));
+        // the host values above are locals: finish the copies before they go out of scope
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    }
+    int r = ensure_keys_all(c);
+    if (!r) r = rebuild_ek(c);
+    if (r) return r;
+    c->steps = h.steps;
+    c->since_sort = (int)h.since_sort;
+    c->energy_fresh = false;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
     return PIC_OK;
 }
 

@@ -38,7 +38,7 @@ class GridDesc(C.Structure):
 
 
 class SpeciesDesc(C.Structure):
-    _fields_ = [("q", C.c_double), ("m", C.c_double)]
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("immobile", C.c_int32)]
 
 
 _VP = C.c_void_p
@@ -55,6 +55,10 @@ SIGNATURES = {
     "pic_set_particles": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
     "pic_set_particles_dev": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
     "pic_count_particles": [_VP, C.c_int, C.POINTER(C.c_int64)],
+    "pic_species_info": [_VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                         C.POINTER(C.c_int64)],
+    "pic_get_state": [_VP, _VP, C.POINTER(C.c_int64)],
+    "pic_set_state": [_VP, _VP, C.c_int64],
     "pic_get_particles": [_VP, C.c_int, C.c_int64, C.POINTER(C.c_int64)] + [_VP] * 8,
     "pic_get_particles_dev": [_VP, C.c_int, C.c_int64, C.POINTER(C.c_int64)] + [_VP] * 8,
     "pic_set_fields": [_VP, _P3, _P3],
@@ -171,7 +175,9 @@ class Simulation:
         return sim
 
     # ------------------------------------------------------------------ particles
-    def add_species(self, q, m, x, y, z, ux, uy, uz, w) -> int:
+    def add_species(self, q, m, x, y, z, ux, uy, uz, w, immobile=False) -> int:
+        """Add a species; immobile=True declares a neutralising background
+        (not stored, not pushed, no current)."""
         arrs = [x, y, z, ux, uy, uz, w]
         dev = _is_dev(x)
         if not dev:
@@ -180,14 +186,37 @@ class Simulation:
             arrs = [a.contiguous().to(self.torch.float64) for a in arrs]
         n = int(arrs[0].shape[0])
         sid = C.c_int(-1)
-        sd = SpeciesDesc(float(q), float(m))
+        sd = SpeciesDesc(float(q), float(m), 1 if immobile else 0)
         f = self.lib.pic_add_species_dev if dev else self.lib.pic_add_species
         self._check(f(self.ctx, C.byref(sd), n, *[_ptr(a) for a in arrs], C.byref(sid)))
         if dev:
             self.stream.synchronize()
         self.nspecies += 1
-        self._tape_ids = getattr(self, "_tape_ids", []) + [n]
         return sid.value
+
+    def species_info(self, species=0) -> dict:
+        q, m, imm, nid = C.c_double(), C.c_double(), C.c_int32(), C.c_int64()
+        self._check(self.lib.pic_species_info(self.ctx, int(species), C.byref(q), C.byref(m), C.byref(imm),
+                                              C.byref(nid)))
+        return {"q": q.value, "m": m.value, "immobile": bool(imm.value), "nid": nid.value}
+
+    def get_state(self) -> bytes:
+        """The whole simulation state as an opaque byte string (checkpoint)."""
+        size = C.c_int64(0)
+        self._check(self.lib.pic_get_state(self.ctx, None, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        self._check(self.lib.pic_get_state(self.ctx, buf, C.byref(size)))
+        return buf.raw[:size.value]
+
+    def set_state(self, blob: bytes):
+        """Restore a state from get_state() of a context with the same grid."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        self._check(self.lib.pic_set_state(self.ctx, buf, len(blob)))
+        n = C.c_int64()
+        k = 0
+        while self.lib.pic_species_info(self.ctx, k, None, None, None, C.byref(n)) == 0:
+            k += 1
+        self.nspecies = k
 
     def set_particles(self, species, x, y, z, ux, uy, uz, w):
         arrs = [x, y, z, ux, uy, uz, w]
@@ -197,7 +226,6 @@ class Simulation:
         n = int(arrs[0].shape[0])
         f = self.lib.pic_set_particles_dev if dev else self.lib.pic_set_particles
         self._check(f(self.ctx, int(species), n, *[_ptr(a) for a in arrs]))
-        self._tape_ids[int(species)] = n
 
     def count(self, species=0) -> int:
         n = C.c_int64()
@@ -312,7 +340,7 @@ class Simulation:
         """dL/d(x, y, z, ux, uy, uz) of the tape's starting particles, in id order."""
         t = self.torch
         if n is None:
-            n = self._tape_ids[species]
+            n = self.species_info(species)["nid"]
         out = [t.zeros(n, dtype=t.float64, device=self.device) for _ in range(6)]
         ptrs = (_VP * 6)(*[o.data_ptr() for o in out])
         self._check(self.lib.pic_tape_particle_grad(self.ctx, int(species), C.addressof(ptrs)))

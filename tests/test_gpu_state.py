@@ -1,0 +1,110 @@
+"""Checkpoint / resume (pic_get_state, pic_set_state) and immobile species.
+
+* A run that is checkpointed after 5 steps and resumed in a fresh context
+  follows the uninterrupted run: fields, current, particles (by id) and
+  energies within 1e-12 after 6 more steps (the only difference is the
+  summation order of the floating-point atomics), FP64 and mixed, with the
+  binned store and the sort phase restored.
+* set_state refuses a blob of another grid descriptor, a truncated blob and
+  a foreign byte string, and leaves the context usable.
+* An immobile species is stored as nothing and changes nothing: a run with
+  electrons plus an immobile background equals the electron-only run.
+"""
+import numpy as np
+import pytest
+
+from paper_1608_01009_gb300 import pic as P
+from paper_1608_01009_gb300 import workloads as W
+from tests import parity as PT
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _two_species():
+    wl = W.uniform_plasma((16, 8, 12), 6, 0.05, 0.2, seed=61)
+    pos = W.uniform_plasma((16, 8, 12), 3, 0.05, 0.1, seed=62, q=1.0, m=1.0)
+    wl.species = wl.species + pos.species
+    return wl
+
+
+def _snapshot(sim, nspecies):
+    E, B = sim.get_fields()
+    J = sim.get_current()
+    parts = []
+    for s in range(nspecies):
+        p = sim.get_particles(s)
+        o = np.argsort(p["id"])
+        parts.append({k: v[o] for k, v in p.items()})
+    return E, B, J, parts, sim.energy()
+
+
+def _compare(a, b, tol):
+    for x, y in zip(a[:3], b[:3]):
+        assert PT.rel_err(x, y) <= tol
+    for pa, pb in zip(a[3], b[3]):
+        assert np.array_equal(pa["id"], pb["id"])
+        for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+            assert PT.rel_err(pa[k], pb[k]) <= tol, k
+    for ea, eb in zip(a[4], b[4]):
+        assert abs(ea - eb) <= tol * abs(eb)
+
+
+@pytest.mark.parametrize("precision,tol", [(P.FP64, 1e-12), (P.MIXED, 1e-6)])
+def test_checkpoint_resume_follows_the_uninterrupted_run(precision, tol):
+    wl = _two_species()
+    a = PT.make_sim(wl, precision=precision)
+    a.step(5)
+    blob = a.get_state()
+    a.step(6)
+    ref = _snapshot(a, 2)
+    b = PT.make_sim(W.uniform_plasma((16, 8, 12), 1, 0.05, 0.0, seed=1), precision=precision)  # other particles
+    b.set_state(blob)
+    assert b.nspecies == 2
+    assert b.species_info(1) == {"q": 1.0, "m": 1.0, "immobile": False, "nid": wl.species[1].n}
+    b.step(6)
+    _compare(_snapshot(b, 2), ref, tol)
+    a.close()
+    b.close()
+
+
+def test_set_state_rejects_foreign_blobs_and_stays_usable():
+    wl = W.config("c1")
+    a = PT.make_sim(wl)
+    a.step(2)
+    blob = a.get_state()
+    other = P.Simulation((16, 16, 8), wl.d, wl.dt)  # another grid
+    with pytest.raises(P.PicError) as ei:
+        other.set_state(blob)
+    assert ei.value.code == -1
+    other.close()
+    with pytest.raises(P.PicError):
+        a.set_state(blob[: len(blob) // 2])
+    with pytest.raises(P.PicError):
+        a.set_state(b"\0" * len(blob))
+    # refused blobs leave the context as it was
+    ref = _snapshot(a, 1)
+    a.set_state(blob)
+    _compare(_snapshot(a, 1), ref, 1e-14)  # energies are re-summed in another order
+    a.step(1)
+    a.sync()
+    a.close()
+
+
+def test_immobile_background_is_not_stored_and_changes_nothing():
+    wl = W.config("c1")
+    sp = wl.species[0]
+    a = PT.make_sim(wl)
+    b = PT.make_sim(wl)
+    ion = b.add_species(1.0, 1836.0, *sp.arrays(), immobile=True)
+    assert ion == 1 and b.count(ion) == 0
+    assert b.species_info(ion)["immobile"]
+    a.step(5)
+    b.step(5)
+    Ea, Ba = a.get_fields()
+    Eb, Bb = b.get_fields()
+    assert PT.rel_err(Eb, Ea) <= 1e-12 and PT.rel_err(Bb, Ba) <= 1e-12
+    assert b.get_particles(ion)["x"].size == 0
+    assert abs(b.energy()[1] - a.energy()[1]) <= 1e-12 * a.energy()[1]
+    a.close()
+    b.close()
