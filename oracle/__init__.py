@@ -21,7 +21,7 @@ _lib = None
 
 class OrGrid(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double), ("bc", C.c_int * 3),
-                ("absorb_cells", C.c_int), ("absorb_sigma", C.c_double)]
+                ("absorb_cells", C.c_int), ("absorb_sigma", C.c_double), ("form_factor", C.c_int)]
 
 
 class OrSpecies(C.Structure):
@@ -71,7 +71,7 @@ def _pp(arrs):
     return ptrs
 
 
-def make_grid(n, d, dt, bc=(0, 0, 0), absorb_cells=8, absorb_sigma=0.1) -> OrGrid:
+def make_grid(n, d, dt, bc=(0, 0, 0), absorb_cells=8, absorb_sigma=0.1, form_factor=1) -> OrGrid:
     g = OrGrid()
     for a in range(3):
         g.n[a] = int(n[a])
@@ -80,6 +80,7 @@ def make_grid(n, d, dt, bc=(0, 0, 0), absorb_cells=8, absorb_sigma=0.1) -> OrGri
     g.dt = float(dt)
     g.absorb_cells = int(absorb_cells)
     g.absorb_sigma = float(absorb_sigma)
+    g.form_factor = int(form_factor)
     return g
 
 
@@ -124,9 +125,10 @@ class Oracle:
     """Whole PIC state on the host, advanced by the oracle's plain loops."""
 
     def __init__(self, n, d, dt, bc=(0, 0, 0), absorb_cells=8, absorb_sigma=0.1, E=None, B=None,
-                 species=()):
+                 species=(), form_factor=1):
         self.n, self.d, self.dt, self.bc = tuple(n), tuple(d), float(dt), tuple(bc)
-        self.grid = make_grid(n, d, dt, bc, absorb_cells, absorb_sigma)
+        self.form_factor = int(form_factor)
+        self.grid = make_grid(n, d, dt, bc, absorb_cells, absorb_sigma, form_factor)
         shape = (3, n[2], n[1], n[0])
         self.E = np.zeros(shape) if E is None else np.array(E, dtype=np.float64, copy=True)
         self.B = np.zeros(shape) if B is None else np.array(B, dtype=np.float64, copy=True)
@@ -134,8 +136,9 @@ class Oracle:
         self.species = [s if isinstance(s, OracleSpecies) else OracleSpecies.from_species(s) for s in species]
 
     @classmethod
-    def from_workload(cls, wl):
-        return cls(wl.n, wl.d, wl.dt, wl.bc, wl.absorb_cells, wl.absorb_sigma, wl.E, wl.B, wl.species)
+    def from_workload(cls, wl, form_factor=1):
+        return cls(wl.n, wl.d, wl.dt, wl.bc, wl.absorb_cells, wl.absorb_sigma, wl.E, wl.B, wl.species,
+                   form_factor=form_factor)
 
     def _f(self, F):
         return _pp([F[0], F[1], F[2]])

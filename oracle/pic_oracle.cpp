@@ -19,6 +19,13 @@
 // standard Yee staggering, with B advanced in two half steps so that E and B
 // both live at integer time levels when the particles are pushed.
 //
+// Beyond the paper (which uses CIC only), form_factor = 2 selects the
+// second-order (triangular-shaped cloud, TSC) form factor -- the quadratic
+// B-spline, weights 1/2 (1/2 - delta)^2, 3/4 - delta^2, 1/2 (1/2 + delta)^2 on
+// the three lattice points nearest the particle -- for both the gather and the
+// charge density, with the charge-conserving current of Esirkepov (Comput.
+// Phys. Commun. 135, 144 (2001)) for an arbitrary form factor.
+//
 // Units are normalised: time 1/w, length c/w, momentum u = p/(mc), fields
 // m c w / e, so that  dE/dt = curl B - J,  dB/dt = -curl E,
 // du/dt = (q/m)(E + u x B / gamma),  dx/dt = u / gamma.
@@ -84,6 +91,7 @@ typedef struct {
     int bc[3];
     int absorb_cells;
     double absorb_sigma;
+    int form_factor;  // 1 (or 0): cloud-in-cell; 2: TSC with the Esirkepov current
 } or_grid;
 
 // One species.  Positions are physical (x in [0, n*d) on periodic axes),
@@ -156,13 +164,48 @@ T interp(const or_grid& g, const T* F, const double off[3], const T xi[3]) {
     return sum;
 }
 
+// Second-order form factor (TSC, quadratic B-spline) weights of a position s
+// (in lattice units) on the lattice points i0-1, i0, i0+1 nearest to it:
+// i0 = floor(s + 1/2), delta = s - i0 in [-1/2, 1/2).
+template <class T>
+long long tsc_weights(T s, T w[3]) {
+    double fl = std::floor(val(s) + 0.5);
+    T delta = s - fl;
+    T a = T(0.5) - delta, b = T(0.5) + delta;
+    w[0] = T(0.5) * a * a;
+    w[1] = T(0.75) - delta * delta;
+    w[2] = T(0.5) * b * b;
+    return (long long)fl;
+}
+
+// TSC interpolation: the 27 lattice points of the component's own staggered
+// lattice around the particle, weighted by the product of the three 1-D
+// quadratic-spline weights.
+template <class T>
+T interp_tsc(const or_grid& g, const T* F, const double off[3], const T xi[3]) {
+    long long i0[3];
+    T w[3][3];
+    for (int a = 0; a < 3; ++a) i0[a] = tsc_weights(T(xi[a] - off[a]), w[a]);
+    T sum = 0.0;
+    for (int c = 0; c < 3; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a)
+                sum += w[0][a] * w[1][b] * w[2][c] * at(g, F, i0[0] - 1 + a, i0[1] - 1 + b, i0[2] - 1 + c);
+    return sum;
+}
+
 template <class T>
 void gather_one(const or_grid& g, T* const E[3], T* const B[3], const T xi[3], T Ep[3], T Bp[3]) {
     for (int c = 0; c < 3; ++c) {
         double oe[3] = {stagE(c, 0), stagE(c, 1), stagE(c, 2)};
         double ob[3] = {stagB(c, 0), stagB(c, 1), stagB(c, 2)};
-        Ep[c] = interp(g, E[c], oe, xi);
-        Bp[c] = interp(g, B[c], ob, xi);
+        if (g.form_factor == 2) {
+            Ep[c] = interp_tsc(g, E[c], oe, xi);
+            Bp[c] = interp_tsc(g, B[c], ob, xi);
+        } else {
+            Ep[c] = interp(g, E[c], oe, xi);
+            Bp[c] = interp(g, B[c], ob, xi);
+        }
     }
 }
 
@@ -266,6 +309,51 @@ void deposit_vb(const or_grid& g, T* J[3], const T xi0[3], const T d[3], const T
             a[e] = pa[e] - double(cell[e]);
         }
         deposit_segment(g, J, cell, a, ds, qfac);
+    }
+}
+
+// Esirkepov's charge-conserving current for the TSC form factor, for the
+// straight move from xi0 by d (positions in cells, |d_a| < 1).  Per axis the
+// old and new 1-D weights S0, S1 live on the 5 nodes base-2 .. base+2 around
+// the old position's nearest node base (the new position's three nodes fall
+// inside since |d| < 1).  The density change S1x S1y S1z - S0x S0y S0z is split
+// into three parts, the x part being
+//   W_x = dSx (S0y S0z + dSy S0z / 2 + S0y dSz / 2 + dSy dSz / 3),  dS = S1 - S0,
+// (y, z cyclic), and the x current on the edge (i+1/2, j, k) is the running
+// sum of -W_x along x from the window's left end: -qfac sum_{i' <= i} W_x, for
+// the 4 edges between the 5 nodes (the sum over all 5 vanishes).  qfac is the
+// same q w / (dt * product of the two transverse cell sizes) as in the VB path.
+template <class T>
+void deposit_esirkepov(const or_grid& g, T* J[3], const T xi0[3], const T d[3], const T qfac[3]) {
+    long long base[3];
+    T S0[3][5], S1[3][5], dS[3][5];
+    for (int a = 0; a < 3; ++a) {
+        T w0[3], w1[3];
+        base[a] = tsc_weights(xi0[a], w0);
+        long long n1 = tsc_weights(T(xi0[a] + d[a]), w1);
+        for (int k = 0; k < 5; ++k) S0[a][k] = S1[a][k] = T(0.0);
+        for (int k = 0; k < 3; ++k) {
+            S0[a][1 + k] = w0[k];
+            S1[a][(int)(n1 - base[a]) + 1 + k] = w1[k];
+        }
+        for (int k = 0; k < 5; ++k) dS[a][k] = S1[a][k] - S0[a][k];
+    }
+    for (int c = 0; c < 3; ++c) {
+        int p = (c + 1) % 3, r = (c + 2) % 3;  // the two transverse axes
+        for (int jp = 0; jp < 5; ++jp)
+            for (int jr = 0; jr < 5; ++jr) {
+                T transverse = S0[p][jp] * S0[r][jr] + T(0.5) * dS[p][jp] * S0[r][jr] +
+                               T(0.5) * S0[p][jp] * dS[r][jr] + dS[p][jp] * dS[r][jr] / T(3.0);
+                T running = 0.0;
+                for (int i = 0; i < 4; ++i) {
+                    running += dS[c][i] * transverse;
+                    long long idx[3];
+                    idx[c] = base[c] - 2 + i;
+                    idx[p] = base[p] - 2 + jp;
+                    idx[r] = base[r] - 2 + jr;
+                    add_at(g, J[c], idx[0], idx[1], idx[2], T(-1.0) * qfac[c] * running);
+                }
+            }
     }
 }
 
@@ -386,7 +474,8 @@ void push_and_deposit(const or_grid& g, T* const E[3], T* const B[3], T* J[3], S
                 int p1 = (c + 1) % 3, p2 = (c + 2) % 3;
                 qfac[c] = sp.q * sp.w[p] / (g.dt * g.d[p1] * g.d[p2]);
             }
-            deposit_vb(g, J, xi0, dcell, qfac);
+            if (g.form_factor == 2) deposit_esirkepov(g, J, xi0, dcell, qfac);
+            else deposit_vb(g, J, xi0, dcell, qfac);
         }
         bool leaves = false;
         for (int a = 0; a < 3; ++a) {
@@ -488,7 +577,8 @@ void or_deposit(const or_grid* g, double* const* J, int64_t n, const double* x0,
         }
         for (int c = 0; c < 3; ++c)
             qfac[c] = q * w[p] / (g->dt * g->d[(c + 1) % 3] * g->d[(c + 2) % 3]);
-        deposit_vb(*g, Jp, xi0, dc, qfac);
+        if (g->form_factor == 2) deposit_esirkepov(*g, Jp, xi0, dc, qfac);
+        else deposit_vb(*g, Jp, xi0, dc, qfac);
     }
 }
 
@@ -529,12 +619,24 @@ double or_field_energy(const or_grid* g, double* const* E, double* const* B) {
 double or_kinetic_energy(const or_species* sp) { return kinetic_energy(as_double(*sp)); }
 
 // Charge density at the nodes (i,j,k) from CIC weights:
-// rho = sum_p q w_p / dV * prod_a (1 - |xi_a - i_a|)_+ .  Added into rho.
+// rho = sum_p q w_p / dV * prod_a (1 - |xi_a - i_a|)_+ , or with form_factor 2
+// from the TSC weights on the 27 nearest nodes.  Added into rho.
 void or_rho(const or_grid* g, const or_species* sp, double* rho) {
     double dV = g->d[0] * g->d[1] * g->d[2];
     for (int64_t p = 0; p < sp->n; ++p) {
         if (!sp->active[p]) continue;
         double xi[3] = {sp->x[p] / g->d[0], sp->y[p] / g->d[1], sp->z[p] / g->d[2]};
+        if (g->form_factor == 2) {
+            double w[3][3];
+            long long i0[3];
+            for (int a = 0; a < 3; ++a) i0[a] = tsc_weights(xi[a], w[a]);
+            for (int c = 0; c < 3; ++c)
+                for (int b = 0; b < 3; ++b)
+                    for (int a = 0; a < 3; ++a)
+                        add_at(*g, rho, i0[0] - 1 + a, i0[1] - 1 + b, i0[2] - 1 + c,
+                               sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][c]));
+            continue;
+        }
         long long i0[3];
         double f[3];
         for (int a = 0; a < 3; ++a) {

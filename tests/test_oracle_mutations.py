@@ -2,8 +2,8 @@
 
 Each case copies oracle/pic_oracle.cpp, plants one plausible mistake (a dropped
 or doubled term, a wrong sign, a swapped index or weight, a missing mass), builds
-the copy on the CPU and runs tests/test_oracle_pins.py against it in a
-subprocess.  The pins are only worth something if every such copy fails them.
+the copy on the CPU and runs tests/test_oracle_pins.py and
+tests/test_oracle_pins_tsc.py against it in a subprocess.  The pins are only worth something if every such copy fails them.
 """
 import os
 import subprocess
@@ -34,6 +34,15 @@ MUTATIONS = [
     ("segment midpoint", "for (int e = 0; e < 3; ++e) m[e] = a[e] + T(0.5) * d[e];",
      "for (int e = 0; e < 3; ++e) m[e] = a[e] + d[e];"),
     ("kinetic energy rest mass", "s += sp.w[p] * (gam - T(1.0));", "s += sp.w[p] * gam;"),
+    # second-order form factor and Esirkepov current
+    ("TSC centre weight", "w[1] = T(0.75) - delta * delta;", "w[1] = T(0.75) + delta * delta;"),
+    ("TSC nearest node", "double fl = std::floor(val(s) + 0.5);", "double fl = std::floor(val(s));"),
+    ("Esirkepov cross term", "dS[p][jp] * dS[r][jr] / T(3.0);", "dS[p][jp] * dS[r][jr] / T(2.0);"),
+    ("Esirkepov half term", "T(0.5) * dS[p][jp] * S0[r][jr]", "dS[p][jp] * S0[r][jr]"),
+    ("Esirkepov current sign", "T(-1.0) * qfac[c] * running", "qfac[c] * running"),
+    ("Esirkepov running sum", "running += dS[c][i] * transverse;", "running = dS[c][i] * transverse;"),
+    ("TSC rho weight", "sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][c])",
+     "sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][b])"),
 ]
 
 
@@ -48,6 +57,7 @@ def test_planted_mistake_fails_pins(label, old, new, tmp_path):
                            str(lib), str(mut)])
     env = dict(os.environ, PIC_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_pins_tsc.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake '%s' passed every pin:\n%s" % (label, r.stdout[-2000:])
