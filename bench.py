@@ -43,6 +43,13 @@ UNIT = "particle-steps/s"
 #   gather 6 trilinear interpolations x 7 lerps x 3 + 3 half-offset adds = 129
 #   Boris push 58, move 16, Villasenor-Buneman (one segment) 57, energy 3.
 FLOPS_PER_PARTICLE = 263
+# Second-order (TSC) form factor with the Esirkepov current, for a move whose
+# 1-D old and new stencils share their 3 nodes on every axis (the common case):
+#   spline weights 2 lattices x 3 axes (48) + offsets (6); 6 separable 27-point
+#   interpolations x 69 = 414; Boris 58, move 16; Esirkepov new weights and dS
+#   45, 3 components x (9 transverse factors x 10 + 18 edges x 3) = 432;
+#   charges, new offsets and energy 12.
+FLOPS_PER_PARTICLE_TSC = 1031
 # Minimum HBM traffic per particle-step of the particle store:
 #   FP64 store: read cell(4) + offset(24) + u(24) + w(8) = 60 B, write cell + offset + u = 52 B.
 #   mixed store: read 4 + 12 + 12 + 4 = 32 B, write 4 + 12 + 12 = 28 B.
@@ -165,10 +172,10 @@ def _workload_desc(wl, precision):
         ", 1% density perturbation" if wl.meta.get("perturb_eps") else "", precision))
 
 
-def time_gpu(torch, pic, wl, precision, steps, warmup, clocks=None, with_timing=True, supercell=4):
+def time_gpu(torch, pic, wl, precision, steps, warmup, clocks=None, with_timing=True, supercell=4, form_factor=1):
     """Device-timed steps of one simulation; returns a result dict."""
     prec = pic.FP64 if precision == "fp64" else pic.MIXED
-    sim = pic.Simulation.from_workload(wl, precision=prec, supercell=supercell)
+    sim = pic.Simulation.from_workload(wl, precision=prec, supercell=supercell, form_factor=form_factor)
     st = sim.stream
     for _ in range(warmup):
         sim.step(1)
@@ -363,11 +370,12 @@ def run_profile_case(args):
     import torch
     torch.cuda.set_device(0)
     from paper_1608_01009_gb300 import pic, workloads as W
-    if args.profile_case == "fp64":
+    ff = 2 if args.profile_case == "tsc" else 1
+    if args.profile_case in ("fp64", "tsc"):
         wl, prec = W.config("c2"), "fp64"
     else:
         wl, prec = W.uniform_plasma((96, 96, 96), 32, 0.05, 0.1, seed=1241, steps=args.steps, name="mixed-96"), "mixed"
-    r = time_gpu(torch, pic, wl, prec, args.steps, args.warmup)
+    r = time_gpu(torch, pic, wl, prec, args.steps, args.warmup, form_factor=ff)
     print(json.dumps({"profile_case": args.profile_case, "workload": _workload_desc(wl, prec),
                       "particle_steps_per_s": r["npart"] * args.steps / (r["ms"] / 1e3),
                       "stage_ms_per_step": {k: round(v, 4) for k, v in r["stage_ms"].items()}}))
@@ -437,6 +445,21 @@ def run_gpu(args):
                         "stage_ms_per_step": {k: round(v, 4) for k, v in r3["stage_ms"].items()},
                         "gpu_launches": r3["launches"], "clocks": clk3.summary()}
         r3["sim"].close()
+    if not args.no_tsc:
+        # second-order form factor + Esirkepov current on the same FP64 workload
+        rt = time_gpu(torch, pic, wl, "fp64", args.steps, args.warmup, form_factor=2)
+        mst = _barrier_max(torch, rt["ms"], ws)
+        pt = rt["stage_ms"]["push_deposit"]
+        tf = FLOPS_PER_PARTICLE_TSC * rt["npart"] / (pt / 1e3) / 1e12
+        out["tsc"] = {"value": weak_value(rt["npart"], ws, args.steps, mst), "unit": UNIT, "dtype": "f64",
+                      "config": {"workload": _workload_desc(wl, "FP64"), "form_factor": "TSC + Esirkepov"},
+                      "ms_per_step": mst / args.steps,
+                      "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_push_tsc",
+                                   "per_launch_ms": pt},
+                      "stage_ms_per_step": {k: round(v, 4) for k, v in rt["stage_ms"].items()},
+                      "gpu_launches": rt["launches"]}
+        rt["sim"].close()
     if not args.no_adjoint:
         out["adjoint"] = time_adjoint(torch, pic, W)
     if not args.no_sweep:
@@ -489,11 +512,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-tsc", action="store_true")
     ap.add_argument("--laser-ramp", action="store_true",
                     help="run the 134 M-particle laser-plasma workload with its 50-step adjoint instead")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "tsc"], default=None,
                     help="run only one reduced case for ncu captures (a few GB on the device): "
-                         "fp64 = the 64^3 x 50 FP64 plasma, mixed = a 96^3 x 32 mixed plasma")
+                         "fp64 = the 64^3 x 50 FP64 plasma, mixed = a 96^3 x 32 mixed plasma, "
+                         "tsc = the 64^3 x 50 plasma with the second-order form factor")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

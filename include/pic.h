@@ -92,6 +92,13 @@ enum { PIC_FP64 = 0, PIC_MIXED = 1 };
  *                 K * max_a(dt / d_a) < 1 (a particle moves less than one cell
  *                 per step along each axis, and the supercell tiles carry one
  *                 cell of slack)
+ *   form_factor   0 or 1: cloud-in-cell with the Villasenor-Buneman current
+ *                 (Sec. 3, the paper's scheme); 2: the second-order
+ *                 (triangular-shaped cloud) form factor, quadratic B-spline
+ *                 weights on the 3 x 3 x 3 nearest lattice points of each
+ *                 staggered component, with Esirkepov's charge-conserving
+ *                 current (PIC_FP64 only; the differentiable-run calls take
+ *                 form factor 1 only)
  *   device        CUDA device ordinal
  *   stream        cudaStream_t the context works on (NULL = legacy default)
  */
@@ -105,6 +112,7 @@ typedef struct {
     int32_t precision;
     int32_t supercell;
     int32_t sort_interval;
+    int32_t form_factor;
     int32_t device;
     void* stream;
 } pic_grid_desc;
@@ -248,7 +256,7 @@ PIC_API int pic_tape_particle_grad(pic_ctx* ctx, int species, double* const dP[6
  * order, with its bin table.  PIC_ERR_ARG if *bytes is too small.
  * pic_set_state restores a blob written by pic_get_state into a context
  * created with the same descriptor (n, d, dt, bc, absorbing layer,
- * precision, supercell, sort_interval; PIC_ERR_ARG otherwise), replacing all
+ * precision, supercell, sort_interval, form factor; PIC_ERR_ARG otherwise), replacing all
  * of its species and dropping a recorded tape; stepping on reproduces the
  * saved run up to the summation order of floating-point atomics.  The blob
  * is a plain byte image for this library build and machine (native byte

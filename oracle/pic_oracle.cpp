@@ -323,20 +323,34 @@ void deposit_vb(const or_grid& g, T* J[3], const T xi0[3], const T d[3], const T
 // sum of -W_x along x from the window's left end: -qfac sum_{i' <= i} W_x, for
 // the 4 edges between the 5 nodes (the sum over all 5 vanishes).  qfac is the
 // same q w / (dt * product of the two transverse cell sizes) as in the VB path.
+// As in the VB path the displacement enters as given: the new offset is taken
+// from the old nearest node, s1 = delta0 + d, and when the nearest node stays
+// the same the weight changes are the exact factored differences of the
+// spline pieces, dS = -d (1 - delta0 - delta1)/2, -d (delta0 + delta1),
+// d (1 + delta0 + delta1)/2 on the nodes -1, 0, +1 (no cancellation of two
+// rounded weights for small d).
 template <class T>
 void deposit_esirkepov(const or_grid& g, T* J[3], const T xi0[3], const T d[3], const T qfac[3]) {
     long long base[3];
-    T S0[3][5], S1[3][5], dS[3][5];
+    T S0[3][5], dS[3][5];
     for (int a = 0; a < 3; ++a) {
         T w0[3], w1[3];
         base[a] = tsc_weights(xi0[a], w0);
-        long long n1 = tsc_weights(T(xi0[a] + d[a]), w1);
-        for (int k = 0; k < 5; ++k) S0[a][k] = S1[a][k] = T(0.0);
-        for (int k = 0; k < 3; ++k) {
-            S0[a][1 + k] = w0[k];
-            S1[a][(int)(n1 - base[a]) + 1 + k] = w1[k];
+        T delta0 = xi0[a] - double(base[a]);
+        T s1 = delta0 + d[a];
+        long long m1 = tsc_weights(s1, w1);  // nearest node of the new position, relative to base
+        for (int k = 0; k < 5; ++k) S0[a][k] = dS[a][k] = T(0.0);
+        for (int k = 0; k < 3; ++k) S0[a][1 + k] = w0[k];
+        if (m1 == 0) {
+            T delta1 = s1;
+            dS[a][1] = T(-0.5) * d[a] * (T(1.0) - delta0 - delta1);
+            dS[a][2] = T(-1.0) * d[a] * (delta0 + delta1);
+            dS[a][3] = T(0.5) * d[a] * (T(1.0) + delta0 + delta1);
+        } else {
+            T S1[5] = {T(0.0), T(0.0), T(0.0), T(0.0), T(0.0)};
+            for (int k = 0; k < 3; ++k) S1[(int)m1 + 1 + k] = w1[k];
+            for (int k = 0; k < 5; ++k) dS[a][k] = S1[k] - S0[a][k];
         }
-        for (int k = 0; k < 5; ++k) dS[a][k] = S1[a][k] - S0[a][k];
     }
     for (int c = 0; c < 3; ++c) {
         int p = (c + 1) % 3, r = (c + 2) % 3;  // the two transverse axes

@@ -33,6 +33,8 @@ cudaError_t count_launch(cudaStream_t, int, const PStore<R>&, const long long*, 
 template <class R>
 cudaError_t kinetic_launch(cudaStream_t, int, const PStore<R>&, const long long*, double, double*);
 cudaError_t energy_finalize_launch(cudaStream_t, const double*, int, const double*, int, double, double*);
+cudaError_t tsc_launch(int, cudaStream_t, const PushParams&, const PStore<double>&, const long long*, const double*,
+                       double*, double*);
 
 // differentiable path (k_adjoint.cu)
 cudaError_t tape_step_launch(cudaStream_t, const TapeDev&, long long, const StepParams&, const double*, double*);
@@ -216,6 +218,9 @@ int validate(const pic_grid_desc* g, pic_ctx* c) {
         return fail(c, PIC_ERR_CFL, "sort_interval %d * max(dt/d) = %.4f must be < 1 (supercell slack is one cell)",
                     g->sort_interval, g->sort_interval * dmax);
     if (g->precision == PIC_MIXED && S % 4) return fail(c, PIC_ERR_ARG, "mixed precision needs supercell 4 or 8");
+    if (g->form_factor < 0 || g->form_factor > 2) return fail(c, PIC_ERR_ARG, "form_factor must be 0, 1 or 2");
+    if (g->form_factor == 2 && g->precision != PIC_FP64)
+        return fail(c, PIC_ERR_ARG, "the second-order form factor runs in FP64 only");
     return PIC_OK;
 }
 
@@ -348,6 +353,16 @@ int push_species(pic_ctx* c, Species& s) {
         e = push_launch<R, 4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
     if (S == 8)
         e = push_launch<R, 8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push launch: %s", cudaGetErrorString(e));
+    c->launches += 1;
+    return PIC_OK;
+}
+
+// Second-order form factor: gather, push, move and Esirkepov current of one
+// species (FP64 only; validated at create).
+int push_species_tsc(pic_ctx* c, Species& s) {
+    PushParams pp = make_params(c, s);
+    cudaError_t e = tsc_launch(c->push_grid, c->st, pp, s.s64.a(), s.d_n, c->EB, c->J, s.d_ek);
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push launch: %s", cudaGetErrorString(e));
     c->launches += 1;
     return PIC_OK;
@@ -683,6 +698,8 @@ int tape_step(pic_ctx* c) {
 
 int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
     if (nsteps < 1 || K < 1) return fail(c, PIC_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+    if (c->desc.form_factor == 2)
+        return fail(c, PIC_ERR_STATE, "the differentiable path implements the cloud-in-cell form factor only");
     Tape& t = c->tape;
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     t.release();
@@ -863,7 +880,7 @@ struct StateHeader {
     char magic[8];
     int32_t precision, supercell, sort_interval, absorb_cells;
     int32_t n[3], bc[3];
-    int32_t nspecies, pad;
+    int32_t nspecies, form_factor;
     double d[3], dt, absorb_sigma;
     int64_t steps, since_sort;
 };
@@ -903,6 +920,7 @@ struct Cursor {
 
 bool same_desc(const StateHeader& h, const pic_grid_desc& d) {
     bool ok = h.precision == d.precision && h.supercell == d.supercell && h.sort_interval == d.sort_interval &&
+              (h.form_factor == 2) == (d.form_factor == 2) &&
               h.absorb_cells == d.absorb_cells && h.dt == d.dt && h.absorb_sigma == d.absorb_sigma;
     for (int a = 0; a < 3; ++a) ok = ok && h.n[a] == d.n[a] && h.bc[a] == d.bc[a] && h.d[a] == d.d[a];
     return ok;
@@ -1142,7 +1160,8 @@ int pic_step(pic_ctx* c, int nsteps) {
         stage_begin(c, 0, &e0);
         for (auto& s : c->sp) {
             if (s.immobile) continue;
-            int r = c->mixed ? push_species<float>(c, s) : push_species<double>(c, s);
+            int r = c->desc.form_factor == 2 ? push_species_tsc(c, s)
+                                             : (c->mixed ? push_species<float>(c, s) : push_species<double>(c, s));
             if (r) return r;
         }
         stage_end(c, 0, e0);
@@ -1270,6 +1289,7 @@ int pic_get_state(pic_ctx* c, void* blob, int64_t* bytes) {
     h.dt = c->desc.dt;
     h.absorb_sigma = c->desc.absorb_sigma;
     h.nspecies = (int32_t)c->sp.size();
+    h.form_factor = c->desc.form_factor == 2 ? 2 : 1;
     h.steps = c->steps;
     h.since_sort = c->since_sort;
     memcpy(at, &h, sizeof h);

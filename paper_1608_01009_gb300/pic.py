@@ -33,7 +33,8 @@ class PicError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("d", C.c_double * 3), ("dt", C.c_double), ("bc", C.c_int32 * 3),
                 ("absorb_cells", C.c_int32), ("absorb_sigma", C.c_double), ("precision", C.c_int32),
-                ("supercell", C.c_int32), ("sort_interval", C.c_int32), ("device", C.c_int32),
+                ("supercell", C.c_int32), ("sort_interval", C.c_int32), ("form_factor", C.c_int32),
+                ("device", C.c_int32),
                 ("stream", C.c_void_p)]
 
 
@@ -117,7 +118,7 @@ class Simulation:
     """
 
     def __init__(self, n, d, dt, bc=(PERIODIC,) * 3, precision=FP64, supercell=4, sort_interval=0, device=0,
-                 absorb_cells=8, absorb_sigma=0.1, stream=None):
+                 absorb_cells=8, absorb_sigma=0.1, stream=None, form_factor=1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the PIC library runs only on the GPU")
@@ -138,6 +139,7 @@ class Simulation:
         g.precision = int(precision)
         g.supercell = int(supercell)
         g.sort_interval = int(sort_interval)
+        g.form_factor = int(form_factor)
         g.device = int(device)
         g.stream = stream.cuda_stream
         self.desc = g
@@ -166,9 +168,9 @@ class Simulation:
             pass
 
     @classmethod
-    def from_workload(cls, wl, precision=FP64, supercell=4, sort_interval=0, device=0, stream=None):
+    def from_workload(cls, wl, precision=FP64, supercell=4, sort_interval=0, device=0, stream=None, form_factor=1):
         sim = cls(wl.n, wl.d, wl.dt, wl.bc, precision, supercell, sort_interval, device, wl.absorb_cells,
-                  wl.absorb_sigma, stream)
+                  wl.absorb_sigma, stream, form_factor)
         sim.set_fields(wl.E, wl.B)
         for sp in wl.species:
             sim.add_species(sp.q, sp.m, *sp.arrays())

@@ -59,6 +59,7 @@ def _desc(**kw):
     g.precision = kw.get("precision", 0)
     g.supercell = kw.get("supercell", 4)
     g.sort_interval = kw.get("sort_interval", 0)
+    g.form_factor = kw.get("form_factor", 1)
     g.device = 0
     g.stream = None
     return g
@@ -77,6 +78,8 @@ def _desc(**kw):
     (dict(bc=(0, 0, 5)), -1),
     (dict(bc=(0, 0, 1), absorb_cells=9), -1),   # layer wider than half the axis
     (dict(absorb_sigma=1.5), -1),
+    (dict(form_factor=3), -1),
+    (dict(form_factor=2, precision=1), -1),     # second order runs in FP64 only
 ])
 def test_create_rejects_bad_descriptors(lib, kw, code):
     ctx = C.c_void_p()

@@ -41,6 +41,8 @@ MUTATIONS = [
     ("Esirkepov half term", "T(0.5) * dS[p][jp] * S0[r][jr]", "dS[p][jp] * S0[r][jr]"),
     ("Esirkepov current sign", "T(-1.0) * qfac[c] * running", "qfac[c] * running"),
     ("Esirkepov running sum", "running += dS[c][i] * transverse;", "running = dS[c][i] * transverse;"),
+    ("Esirkepov factored centre change", "dS[a][2] = T(-1.0) * d[a] * (delta0 + delta1);",
+     "dS[a][2] = T(-1.0) * d[a] * (delta0 - delta1);"),
     ("TSC rho weight", "sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][c])",
      "sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][b])"),
 ]
