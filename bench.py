@@ -65,9 +65,9 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _kernel_hash():
+def _kernel_hash(kind="fp64"):
     h = hashlib.sha256()
-    for f in ("k_push.cu", "pic_internal.cuh"):
+    for f in ("k_tsc.cu" if kind == "tsc" else "k_push.cu", "pic_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1608_01009_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -80,7 +80,7 @@ def _traffic(kind):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
         r = rec.get(kind)
-        if r and r.get("kernel_sha") == _kernel_hash():
+        if r and r.get("kernel_sha") == _kernel_hash(kind):
             return r["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -455,7 +455,7 @@ def run_gpu(args):
                       "config": {"workload": _workload_desc(wl, "FP64"), "form_factor": "TSC + Esirkepov"},
                       "ms_per_step": mst / args.steps,
                       "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                   "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_push_tsc",
+                                   "frac": tf / FP64_PEAK_TFLOPS, "traffic": _traffic("tsc"), "kernel": "k_push_tsc",
                                    "per_launch_ms": pt},
                       "stage_ms_per_step": {k: round(v, 4) for k, v in rt["stage_ms"].items()},
                       "gpu_launches": rt["launches"]}
