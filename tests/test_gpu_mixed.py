@@ -20,7 +20,8 @@ from tests import parity as PT
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# where to write the measured error record (optional; set to keep the figures)
+OUT = os.environ.get("PICGB_TEST_RECORD_DIR")
 
 
 def _one_step_errors(wl, warm=0, supercell=4):
@@ -76,9 +77,10 @@ def test_mixed_field_energy_after_100_steps():
     rec = {"steps": 100, "field_energy_rel_err_mixed": {"50": float(err_mixed[49]), "100": float(err_mixed[99]),
                                                         "max": float(err_mixed.max())},
            "field_energy_rel_err_fp64": {"100": float(err_fp64[99]), "max": float(err_fp64.max())}}
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "mixed_energy_error.json"), "w") as f:
-        json.dump(rec, f, indent=1)
+    if OUT:
+        os.makedirs(OUT, exist_ok=True)
+        with open(os.path.join(OUT, "mixed_energy_error.json"), "w") as f:
+            json.dump(rec, f, indent=1)
     # the FP64 GPU path tracks the oracle to reordering noise
     assert err_fp64.max() < 1e-9, rec
     # the mixed path's stated target: 1e-5 relative in field energy after 100 steps
