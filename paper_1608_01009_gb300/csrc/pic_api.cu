@@ -21,7 +21,7 @@ cudaError_t field_energy_launch(cudaStream_t, const double*, const GridDev&, dou
 int fdtd_blocks(const GridDev&);
 template <class R>
 cudaError_t sort_launch(cudaStream_t, int, const GridDev&, PStore<R>, PStore<R>, const long long*, long long*, int*,
-                        int*, int*, int*, int*, Chunk*, int*);
+                        int*, int*, int*, Chunk*, int*);
 long long sort_tiles(long long nkeys);
 template <class R>
 cudaError_t load_launch(cudaStream_t, long long, const double* const*, const PStore<R>&, const GridDev&);
@@ -135,8 +135,6 @@ struct pic_ctx {
     XQueue<float> xq32{};
     std::vector<Species> sp;
     int* d_err = nullptr;
-    int* d_keys = nullptr;
-    long long keys_cap = 0;
     int* d_counts = nullptr;    // per-cell histogram of the sort (ncell)
     int* d_cursor = nullptr;    // per-cell scatter cursor (ncell)
     int* d_tile_sum = nullptr;  // per-tile totals of the sort's scan
@@ -299,7 +297,7 @@ Store<float>& store_of<float>(Species& s) { return s.s32; }
 template <class R>
 int sort_species(pic_ctx* c, Species& s) {
     Store<R>& st = store_of<R>(s);
-    cudaError_t e = sort_launch<R>(c->st, c->nsm, c->g, st.a(), st.b(), s.d_n, s.d_n + 1, c->d_keys, c->d_counts,
+    cudaError_t e = sort_launch<R>(c->st, c->nsm, c->g, st.a(), st.b(), s.d_n, s.d_n + 1, c->d_counts,
                                    c->d_cursor, c->d_tile_sum, s.d_bin_start, s.d_chunks, s.d_nchunks);
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "sort launch: %s", cudaGetErrorString(e));
     c->launches += 5;
@@ -388,21 +386,6 @@ void free_species(Species& s) {
     s.allocs.clear();
 }
 
-int ensure_keys(pic_ctx* c, long long n) {
-    if (n <= c->keys_cap) return PIC_OK;
-    if (c->d_keys) {
-        cudaStreamSynchronize(c->st);
-        cudaFree(c->d_keys);
-        for (auto& p : c->allocs)
-            if (p == c->d_keys) p = nullptr;
-        c->d_keys = nullptr;
-    }
-    int r = dalloc(c, c->allocs, &c->d_keys, (size_t)n);
-    if (r) return r;
-    c->keys_cap = n;
-    return PIC_OK;
-}
-
 // (Re)allocate the store and bin tables of species s for n particles.
 int alloc_species(pic_ctx* c, Species& s, long long n) {
     cudaStreamSynchronize(c->st);
@@ -419,13 +402,6 @@ int alloc_species(pic_ctx* c, Species& s, long long n) {
     return PIC_OK;
 }
 
-// Sort keys for the largest species.
-int ensure_keys_all(pic_ctx* c) {
-    long long kmax = 1;
-    for (auto& o : c->sp) kmax = o.cap > kmax ? o.cap : kmax;
-    return ensure_keys(c, kmax);
-}
-
 // (Re)load the particles of species s from FP64 arrays (host or device).
 int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src, bool device) {
     if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", n);
@@ -435,8 +411,7 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
         int r = alloc_species(c, s, n);
         if (r) return r;
     }
-    int r = ensure_keys_all(c);
-    if (r) return r;
+    int r = PIC_OK;
     // stage FP64 inputs on the device when they come from the host
     const double* dsrc[7];
     if (!device && n > 0) {
@@ -1394,8 +1369,7 @@ int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
         // the host values above are locals: finish the copies before they go out of scope
         CUDA_TRY(c, cudaStreamSynchronize(c->st));
     }
-    int r = ensure_keys_all(c);
-    if (!r) r = rebuild_ek(c);
+    int r = rebuild_ek(c);
     if (r) return r;
     c->steps = h.steps;
     c->since_sort = (int)h.since_sort;
