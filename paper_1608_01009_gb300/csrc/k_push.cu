@@ -53,11 +53,19 @@ __device__ __forceinline__ R lerp(R a, R b, R t) {
 // interpolation is then 2 vector loads and 2 x 3 FMAs + 1 lerp, instead of 8
 // scalar loads and 7 lerps (14 operations).  FP32: one float4 per cell; FP64:
 // two double2.  S = 8 keeps the raw tile (its coefficient tile would not fit).
+#ifndef PICGB_MOMENTS
+#define PICGB_MOMENTS 1
+#endif
 template <class R, int S>
 struct Tile {
-    static constexpr int T = S + 4, T3 = T * T * T;
+    static constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
     static constexpr int NE = (T - 1) * (T - 1) * T;  // coefficient cells per component
     static constexpr bool kCoef = S <= 4;
+    // FP64 with a coefficient tile accumulates the deposit's 12 moments per
+    // cell (see value_offset) instead of the 3 edge components
+    static constexpr bool kMoments = PICGB_MOMENTS && sizeof(R) == 8 && kCoef;
+    static constexpr int ACC = kMoments ? 12 * TJ3 : 3 * TJ3;         // accumulation tile (elements)
+    static constexpr int RAW = 6 * T3 > ACC ? 6 * T3 : ACC;           // raw tile region, re-used for it
 };
 
 template <class R>
@@ -197,12 +205,26 @@ __device__ __forceinline__ int edge_offset(int m) {
     return comp * TJ * TJ * TJ + (e & 1) * (comp == 0 ? TJ : 1) + (e >> 1) * (comp == 2 ? TJ : TJ * TJ);
 }
 
+// Moment form of the deposit (FP64 kernel with a coefficient tile).  With p,
+// r the transverse axes of component c in the order of (s1, s2) above, the
+// four edge values of a segment are linear in four moments,
+//   A = Q d_c,  B = A m_p,  C = A m_r,  D = B m_r + Q sigma-term,
+//   (0,0): A - B - C + D,  (1,0): B - D,  (0,1): C - D,  (1,1): D,
+// so the tile accumulates the 12 moments per cell (5 FP64 operations per
+// component instead of 8) and the merge forms each edge value from the four
+// cells around it.  Value m of a cell lives at m * TJ^3 + cell key.
+template <bool M, int TJ>
+__device__ __forceinline__ int value_offset(int m) {
+    if constexpr (M) return m * TJ * TJ * TJ;
+    else return edge_offset<TJ>(m);
+}
+
 // Per distinct key of the warp: the lanes holding it contribute their v, the
 // rest zeros, one reduce-scatter, 12 owner lanes add the totals to the tile.
-template <class R, int TJ>
+template <class R, int TJ, bool M>
 __device__ __forceinline__ void deposit_by_key(R* Jt, int key, const R (&v)[12]) {
     const int lane = threadIdx.x & 31;
-    const int eo = edge_offset<TJ>(reduce12_index(lane));
+    const int eo = value_offset<M, TJ>(reduce12_index(lane));
     const bool owner = reduce12_owner(lane);
     unsigned todo = __ballot_sync(FULL, key >= 0);
     while (todo) {
@@ -241,15 +263,22 @@ struct DepositCost {
 // key are summed in the warp before the shared-memory atomics: by one
 // reduce-scatter per distinct key when the warp holds few keys, else by a
 // segmented scan whose last lane per run adds the run's 12 totals.
-template <class R, int TJ>
+template <class R, int TJ, bool M>
 __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy,
                                                 R Qz) {
-    constexpr int TJ2 = TJ * TJ, TJ3 = TJ * TJ * TJ;
     const R h = R(0.5), tw = R(1.0 / 12.0);
     const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
-    const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
     const R vol = dx * dy * (dz * tw);  // sigma term d_x d_y d_z / 12, shared by the 3 components
     R v[12];
+    if constexpr (M) {  // moments A, B, C, D per component (transverse axes y,z; x,z; x,y)
+        const R qx = Qx * dx, bx = qx * my;
+        v[0] = qx, v[1] = bx, v[2] = qx * mz, v[3] = fma(bx, mz, Qx * vol);
+        const R qy = Qy * dy, by = qy * mx;
+        v[4] = qy, v[5] = by, v[6] = qy * mz, v[7] = fma(by, mz, Qy * vol);
+        const R qz = Qz * dz, bz = qz * mx;
+        v[8] = qz, v[9] = bz, v[10] = qz * my, v[11] = fma(bz, my, Qz * vol);
+    } else {
+    const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
     {  // Jx on edges (i+1/2, j+s1, k+s2)
         const R q = Qx * dx, qc = Qx * vol, qo = q * oy, qm = q * my;
         v[0] = fma(qo, oz, qc);
@@ -271,6 +300,7 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
         v[10] = fma(qo, my, -qc);
         v[11] = fma(qm, my, qc);
     }
+    }
     const int lane = threadIdx.x & 31;
     const int kprev = __shfl_up_sync(FULL, key, 1);
     const int knext = __shfl_down_sync(FULL, key, 1);
@@ -283,7 +313,7 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
     const int nruns = __popc(__ballot_sync(FULL, head && key >= 0));
     const int rounds = longest > 1 ? 32 - __clz(longest - 1) : 0;
     if (DepositCost<R>::channels_win(nruns, rounds)) {
-        deposit_by_key<R, TJ>(Jt, key, v);
+        deposit_by_key<R, TJ, M>(Jt, key, v);
         return;
     }
     for (int dd = 1; dd < longest; dd <<= 1) {
@@ -294,33 +324,39 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
         }
     }
     if (tail && key >= 0) {
-        R* J = Jt + key;
-        atomicAdd(J, v[0]);
-        atomicAdd(J + TJ, v[1]);
-        atomicAdd(J + TJ2, v[2]);
-        atomicAdd(J + TJ + TJ2, v[3]);
-        J += TJ3;
-        atomicAdd(J, v[4]);
-        atomicAdd(J + 1, v[5]);
-        atomicAdd(J + TJ2, v[6]);
-        atomicAdd(J + 1 + TJ2, v[7]);
-        J += TJ3;
-        atomicAdd(J, v[8]);
-        atomicAdd(J + 1, v[9]);
-        atomicAdd(J + TJ, v[10]);
-        atomicAdd(J + 1 + TJ, v[11]);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) atomicAdd(Jt + key + value_offset<M, TJ>(i), v[i]);
     }
 }
 
 // Current of one piece with plain shared atomics (the deferred crossing moves
 // of different lanes belong to different particles, rarely to the same cell).
-template <class R, int TJ>
+template <class R, int TJ, bool M>
 __device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy, R Qz) {
     constexpr int TJ2 = TJ * TJ, TJ3 = TJ * TJ * TJ;
     const R h = R(0.5), tw = R(1.0 / 12.0);
     const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
-    const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
     const R vol = dx * dy * (dz * tw);  // sigma term d_x d_y d_z / 12, shared by the 3 components
+    if constexpr (M) {
+        R* J = Jt + b;
+        const R qx = Qx * dx, bx = qx * my;
+        atomicAdd(J, qx);
+        atomicAdd(J + TJ3, bx);
+        atomicAdd(J + 2 * TJ3, qx * mz);
+        atomicAdd(J + 3 * TJ3, fma(bx, mz, Qx * vol));
+        const R qy = Qy * dy, by = qy * mx;
+        atomicAdd(J + 4 * TJ3, qy);
+        atomicAdd(J + 5 * TJ3, by);
+        atomicAdd(J + 6 * TJ3, qy * mz);
+        atomicAdd(J + 7 * TJ3, fma(by, mz, Qy * vol));
+        const R qz = Qz * dz, bz = qz * mx;
+        atomicAdd(J + 8 * TJ3, qz);
+        atomicAdd(J + 9 * TJ3, bz);
+        atomicAdd(J + 10 * TJ3, qz * my);
+        atomicAdd(J + 11 * TJ3, fma(bz, my, Qz * vol));
+        return;
+    }
+    const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
     {
         const R q = Qx * dx, qc = Qx * vol, qo = q * oy, qm = q * my;
         R* J = Jt + b;
@@ -351,7 +387,7 @@ __device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R d
 // k0 in the J tile, start offset a, displacement d): cut at every face crossed
 // (at most one per axis), pieces in order of the crossing parameter, each
 // piece deposited in the cell that holds its midpoint.
-template <class R, int TJ>
+template <class R, int TJ, bool M>
 __device__ void split_direct(R* Jt, int k0, R ax, R ay, R az, R dx, R dy, R dz, R Qx, R Qy, R Qz) {
     const R bx = ax + dx, by = ay + dy, bz = az + dz;
     const int sx = cell_shift(bx), sy = cell_shift(by), sz = cell_shift(bz);
@@ -369,7 +405,7 @@ __device__ void split_direct(R* Jt, int k0, R ax, R ay, R az, R dx, R dy, R dz, 
         const R ddx = dt * dx, ddy = dt * dy, ddz = dt * dz;
         const int ox = cell_shift(fma(R(0.5), ddx, pax)), oy = cell_shift(fma(R(0.5), ddy, pay)),
                   oz = cell_shift(fma(R(0.5), ddz, paz));
-        piece_direct<R, TJ>(Jt, ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox), pax - R(ox), pay - R(oy), paz - R(oz),
+        piece_direct<R, TJ, M>(Jt, ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox), pax - R(ox), pay - R(oy), paz - R(oz),
                             ddx, ddy, ddz, Qx, Qy, Qz);
     }
 }
@@ -398,7 +434,7 @@ __device__ __forceinline__ void warp_queue_flush(R* Jt, const R* q, int n, const
     const int lane = threadIdx.x & 31;
     if (lane < n) {
         const R w = q[7 * WQ + lane];
-        split_direct<R, TJ>(Jt, __float_as_int(q[lane]), q[WQ + lane], q[2 * WQ + lane], q[3 * WQ + lane],
+        split_direct<R, TJ, false>(Jt, __float_as_int(q[lane]), q[WQ + lane], q[2 * WQ + lane], q[3 * WQ + lane],
                             q[4 * WQ + lane], q[5 * WQ + lane], q[6 * WQ + lane], pp.cq_f[0] * w, pp.cq_f[1] * w,
                             pp.cq_f[2] * w);
     }
@@ -412,6 +448,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
                                        const PushParams& pp, int c0x, int c0y, int c0z, int* err,
                                        const XQueue<R>& xq, int qbase, int* s_qn, R* wqueue, int& wq_n) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
+    constexpr bool kMom = Tile<R, S>::kMoments;
     const GridDev& g = pp.g;
     const int cp = valid ? ps.cell[p] : INACTIVE;
     bool act = cp >= 0;  // negative: no particle, or deactivated at an absorbing boundary
@@ -505,7 +542,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
         // warps; moves that stay in their cell deposit one segment each, summed per
         // cell run
         const bool cross = dep && (sx | sy | sz) != 0;
-        deposit_segment<R, TJ>(Jt, dep && !cross ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+        deposit_segment<R, TJ, kMom>(Jt, dep && !cross ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
         const unsigned cm = __ballot_sync(FULL, cross);
         if (cm) {
             const int lane = threadIdx.x & 31, first = __ffs(cm) - 1;
@@ -526,12 +563,12 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
         }
     } else if constexpr (WarpQueue<R, S, NT>::kOn) {
         const bool cross = dep && (sx | sy | sz) != 0;
-        deposit_segment<R, TJ>(Jt, dep && !cross ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+        deposit_segment<R, TJ, kMom>(Jt, dep && !cross ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
         const unsigned cm = __ballot_sync(FULL, cross);
         if (cm) {
             const int cnt = __popc(cm), lane = threadIdx.x & 31;
             if (cnt >= 16) {
-                if (cross) split_direct<R, TJ>(Jt, key0, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+                if (cross) split_direct<R, TJ, false>(Jt, key0, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
             } else {
                 if (wq_n + cnt > WQ) {
                     warp_queue_flush<R, TJ>(Jt, wqueue, wq_n, pp);
@@ -556,7 +593,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
         // summed per cell run like a whole move
         const int nseg = 1 + (sx != 0) + (sy != 0) + (sz != 0);
         if (!__any_sync(FULL, dep && nseg > 1)) {
-            deposit_segment<R, TJ>(Jt, dep ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
+            deposit_segment<R, TJ, false>(Jt, dep ? key0 : -1, fx, fy, fz, dx, dy, dz, Qx, Qy, Qz);
         } else {
             R t1 = R(1), t2 = R(1), t3 = R(1);
             if (sx) t1 = cross_t(R(sx > 0 ? 1 : 0) - fx, dx);
@@ -564,7 +601,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
             if (sz) t3 = cross_t(R(sz > 0 ? 1 : 0) - fz, dz);
             sort3(t1, t2, t3);
             // first piece [0, t1]: starts at the offset itself and stays in the start cell
-            deposit_segment<R, TJ>(Jt, dep ? key0 : -1, fx, fy, fz, t1 * dx, t1 * dy, t1 * dz, Qx, Qy, Qz);
+            deposit_segment<R, TJ, false>(Jt, dep ? key0 : -1, fx, fy, fz, t1 * dx, t1 * dy, t1 * dz, Qx, Qy, Qz);
             const int jx = lx + 1, jy = ly + 1, jz = lz + 1;
 #pragma unroll
             for (int s = 1; s < 4; ++s) {
@@ -577,7 +614,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
                 const R ddx = dt * dx, ddy = dt * dy, ddz = dt * dz;
                 const int ox = cell_shift(fma(R(0.5), ddx, pax)), oy = cell_shift(fma(R(0.5), ddy, pay)),
                           oz = cell_shift(fma(R(0.5), ddz, paz));
-                deposit_segment<R, TJ>(Jt, on ? ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox) : -1, pax - R(ox),
+                deposit_segment<R, TJ, false>(Jt, on ? ((jz + oz) * TJ + (jy + oy)) * TJ + (jx + ox) : -1, pax - R(ox),
                                        pay - R(oy), paz - R(oz), ddx, ddy, ddz, Qx, Qy, Qz);
             }
         }
@@ -628,8 +665,10 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
     extern __shared__ unsigned char smem_raw[];
     // smem: raw TMA tile (re-used as the J tile once the coefficients are built) | coefficient tile
     R* F = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    constexpr bool kMom = Tile<R, S>::kMoments;
+    constexpr int ACC = Tile<R, S>::ACC, RAW = Tile<R, S>::RAW;
     R* Jt = kCoef ? F : F + 6 * T3;
-    Coef<R>* X = reinterpret_cast<Coef<R>*>(F + 6 * T3);
+    Coef<R>* X = reinterpret_cast<Coef<R>*>(F + RAW);
     const void* Fuse = kCoef ? static_cast<const void*>(X) : static_cast<const void*>(F);
     __shared__ uint64_t bar;
     __shared__ double red[NT / 32];
@@ -669,7 +708,7 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         if (kCoef) {
             build_coef<R, T, NT>(F, X);
             __syncthreads();
-            for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);  // J tile over the raw tile
+            for (int i = threadIdx.x; i < ACC; i += NT) Jt[i] = R(0);  // J tile over the raw tile
             __syncthreads();
         }
         const int end = ch.start + ch.count;
@@ -690,7 +729,7 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         for (int i = threadIdx.x; i < nq; i += NT) {
             const int q = qbase + i;
             const R w = xq.w[q];
-            split_direct<R, TJ>(Jt, xq.key[q], xq.a[0][q], xq.a[1][q], xq.a[2][q], xq.d[0][q], xq.d[1][q], xq.d[2][q],
+            split_direct<R, TJ, kMom>(Jt, xq.key[q], xq.a[0][q], xq.a[1][q], xq.a[2][q], xq.d[0][q], xq.d[1][q], xq.d[2][q],
                                 prm<R>(pp.cq[0], pp.cq_f[0]) * w, prm<R>(pp.cq[1], pp.cq_f[1]) * w,
                                 prm<R>(pp.cq[2], pp.cq_f[2]) * w);
         }
@@ -698,10 +737,24 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         if (threadIdx.x == 0) s_qn = 0;
         // merge: J tile cell t is domain cell c0 - 1 + t, padded index c0 + 1 + t
         for (int i = threadIdx.x; i < 3 * TJ3; i += NT) {
-            const R v = Jt[i];
+            const int comp = i / TJ3, r = i - comp * TJ3;
+            const int tz = r / (TJ * TJ), ty = (r / TJ) % TJ, tx = r % TJ;
+            R v;
+            if constexpr (kMom) {
+                // edge value from the moments of the (up to) four cells around it:
+                // (0,0) A - B - C + D of the cell, (1,0) B - D of the cell one step
+                // down the first transverse axis, (0,1) C - D down the second, (1,1) D
+                const R* Mc = Jt + 4 * comp * TJ3;
+                const int sp = comp == 0 ? TJ : 1, sr = comp == 2 ? TJ : TJ * TJ;
+                const bool hp = (comp == 0 ? ty : tx) > 0, hr = (comp == 2 ? ty : tz) > 0;
+                v = (Mc[r] - Mc[TJ3 + r]) + (Mc[3 * TJ3 + r] - Mc[2 * TJ3 + r]);
+                if (hp) v += Mc[TJ3 + r - sp] - Mc[3 * TJ3 + r - sp];
+                if (hr) v += Mc[2 * TJ3 + r - sr] - Mc[3 * TJ3 + r - sr];
+                if (hp && hr) v += Mc[3 * TJ3 + r - sp - sr];
+            } else {
+                v = Jt[i];
+            }
             if (v != R(0)) {
-                const int comp = i / TJ3, r = i - comp * TJ3;
-                const int tz = r / (TJ * TJ), ty = (r / TJ) % TJ, tx = r % TJ;
                 const long long o = (long long)comp * g.P + (c0x + 1 + tx) +
                                     (long long)g.np[0] * ((c0y + 1 + ty) + (long long)g.np[1] * (c0z + 1 + tz));
                 atomicAdd(&J[o], (double)v);
@@ -722,7 +775,7 @@ constexpr int PUSH_NT = PICGB_PUSH_NT;
 template <class R, int S>
 size_t push_smem_bytes() {
     constexpr int T = S + 4, TJ = S + 3;
-    if (Tile<R, S>::kCoef) return 128 + sizeof(R) * 6 * T * T * T + sizeof(Coef<R>) * 6 * Tile<R, S>::NE;
+    if (Tile<R, S>::kCoef) return 128 + sizeof(R) * Tile<R, S>::RAW + sizeof(Coef<R>) * 6 * Tile<R, S>::NE;
     return 128 + sizeof(R) * (6 * T * T * T + 3 * TJ * TJ * TJ);
 }
 
