@@ -443,7 +443,9 @@ __device__ __forceinline__ void warp_queue_flush(R* Jt, const R* q, int n, const
 
 // One particle per lane; all 32 lanes of the warp call it (lanes without a
 // particle pass valid = false).  Returns w (gamma - 1) of the new state.
-template <class R, int S, int NT>
+// CU: cubic cells, so dt/d and the current factor q/(dt d d) are the same on
+// every axis (one multiply each instead of three).
+template <class R, int S, int NT, bool CU>
 __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const PStore<R>& ps, int p, bool valid,
                                        const PushParams& pp, int c0x, int c0y, int c0z, int* err,
                                        const XQueue<R>& xq, int qbase, int* s_qn, R* wqueue, int& wq_n) {
@@ -518,8 +520,14 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     // ---- move: displacement in cells, x^{n+1} = x^n + dt u / gamma
     const R u2p1 = fma(ux, ux, fma(uy, uy, fma(uz, uz, R(1))));
     const R gi = rsqrt(u2p1);
-    const R dx = ux * (gi * prm<R>(pp.dtd[0], pp.dtd_f[0])), dy = uy * (gi * prm<R>(pp.dtd[1], pp.dtd_f[1])),
-            dz = uz * (gi * prm<R>(pp.dtd[2], pp.dtd_f[2]));
+    R dx, dy, dz;
+    if constexpr (CU) {
+        const R gd = gi * prm<R>(pp.dtd[0], pp.dtd_f[0]);
+        dx = ux * gd, dy = uy * gd, dz = uz * gd;
+    } else {
+        dx = ux * (gi * prm<R>(pp.dtd[0], pp.dtd_f[0])), dy = uy * (gi * prm<R>(pp.dtd[1], pp.dtd_f[1])),
+        dz = uz * (gi * prm<R>(pp.dtd[2], pp.dtd_f[2]));
+    }
     const R bx = fx + dx, by = fy + dy, bz = fz + dz;  // end point in the start cell's frame
     const int sx = cell_shift(bx), sy = cell_shift(by), sz = cell_shift(bz);
     if (act && ((unsigned)(lx + sx + 1) > (unsigned)(S + 1) || (unsigned)(ly + sy + 1) > (unsigned)(S + 1) ||
@@ -533,8 +541,8 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     // ---- Villasenor-Buneman deposit into the shared J tile (tile origin = cell c0-1)
     const bool dep = act && w != R(0);
     const R wq = dep ? w : R(0);
-    const R Qx = prm<R>(pp.cq[0], pp.cq_f[0]) * wq, Qy = prm<R>(pp.cq[1], pp.cq_f[1]) * wq,
-            Qz = prm<R>(pp.cq[2], pp.cq_f[2]) * wq;
+    const R Qx = prm<R>(pp.cq[0], pp.cq_f[0]) * wq;
+    const R Qy = CU ? Qx : prm<R>(pp.cq[1], pp.cq_f[1]) * wq, Qz = CU ? Qx : prm<R>(pp.cq[2], pp.cq_f[2]) * wq;
     const int key0 = ((lz + 1) * TJ + (ly + 1)) * TJ + (lx + 1);
     if constexpr (sizeof(R) == 8) {
         // FP64: a crossing lane would make its whole warp execute the split on the
@@ -655,7 +663,7 @@ constexpr int push_min_blocks() {
     return sizeof(R) == 4 ? PICGB_PUSH_MINB_F32 : 2;
 }
 
-template <class R, int S, int NT>
+template <class R, int S, int NT, bool CU>
 __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<R> ps,
                                             XQueue<R> xq, const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
                                             double* __restrict__ J, double* __restrict__ ek_part,
@@ -715,7 +723,7 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         R ek_chunk = R(0);  // at most CHUNK / NT particles per lane
         for (int base = ch.start + warp * 32; base < end; base += NT) {
             const int p = base + lane;
-            ek_chunk += push_lane<R, S, NT>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err, xq, qbase, &s_qn,
+            ek_chunk += push_lane<R, S, NT, CU>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err, xq, qbase, &s_qn,
                                             wqueue, wq_n);
         }
         if constexpr (WarpQueue<R, S, NT>::kOn) {
@@ -781,19 +789,25 @@ size_t push_smem_bytes() {
 
 template <class R, int S>
 cudaError_t push_setup(int* blocks_per_sm) {
-    auto k = k_push<R, S, PUSH_NT>;
-    size_t sm = push_smem_bytes<R, S>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int sm = (int)push_smem_bytes<R, S>();
+    cudaError_t e = cudaFuncSetAttribute(k_push<R, S, PUSH_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_push<R, S, PUSH_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, PUSH_NT, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R, S, PUSH_NT, false>, PUSH_NT, sm);
 }
 
 template <class R, int S>
 cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
                         const XQueue<R>& xq, const Chunk* chunks, const int* nchunks, double* J, double* ek_part,
                         int* err) {
-    k_push<R, S, PUSH_NT><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, xq, chunks, nchunks, J,
-                                                                         ek_part, err);
+    const bool cubic = pp.g.d[0] == pp.g.d[1] && pp.g.d[1] == pp.g.d[2];
+    if (cubic)
+        k_push<R, S, PUSH_NT, true><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, xq, chunks, nchunks, J,
+                                                                               ek_part, err);
+    else
+        k_push<R, S, PUSH_NT, false><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, xq, chunks, nchunks,
+                                                                                J, ek_part, err);
     return cudaGetLastError();
 }
 
