@@ -99,22 +99,23 @@ def uniform_plasma(n=(16, 16, 16), ppc=8, delta=0.05, vth=0.05, density=1.0, see
                    q=-1.0, m=1.0) -> Workload:
     """Uniform periodic thermal electron plasma, ppc electrons drawn uniformly in
     every cell, each momentum component vth * N(0, 1), zero initial fields.
+    delta: the cell size, one value (cubic cells) or one per axis.
 
     perturb_eps > 0 displaces x by (eps / k) cos(k x) with k = 2 pi / Lx
     (mode 1), which gives a density n (1 + eps sin k x) to first order.
     """
     rng = np.random.default_rng(seed)
-    d = (delta, delta, delta)
+    d = tuple(float(v) for v in np.broadcast_to(np.asarray(delta, dtype=np.float64), (3,)))
     cells = _cells_repeated(n, ppc)
     npart = cells.shape[0]
-    pos = (cells + rng.random((npart, 3))) * delta
+    pos = (cells + rng.random((npart, 3))) * np.array(d)
     if perturb_eps:
-        Lx = n[0] * delta
+        Lx = n[0] * d[0]
         k = 2.0 * math.pi / Lx
         x = pos[:, 0] + (perturb_eps / k) * np.cos(k * pos[:, 0])
         pos[:, 0] = np.mod(x, Lx)
     u = vth * rng.standard_normal((npart, 3))
-    w = np.full(npart, density * delta ** 3 / ppc)
+    w = np.full(npart, density * d[0] * d[1] * d[2] / ppc)
     sp = Species(q, m, pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy(),
                  u[:, 0].copy(), u[:, 1].copy(), u[:, 2].copy(), w)
     shape = (3, n[2], n[1], n[0])

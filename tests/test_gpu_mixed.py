@@ -37,6 +37,14 @@ def _one_step_errors(wl, warm=0, supercell=4):
     return errs
 
 
+def test_mixed_one_step_non_cubic_cells():
+    errs = _one_step_errors(W.uniform_plasma((16, 8, 24), 5, (0.05, 0.06, 0.045), 0.25, seed=22), warm=3)
+    assert max(errs[k] for k in ("x", "y", "z")) < 1e-7, errs
+    assert max(errs[k] for k in ("ux", "uy", "uz")) < 1e-6, errs
+    assert max(errs[k] for k in ("Jx", "Jy", "Jz")) < 1e-5, errs
+    assert max(errs[k] for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")) < 1e-6, errs
+
+
 @pytest.mark.parametrize("S", [4, 8])
 def test_mixed_one_step_c1(S):
     errs = _one_step_errors(W.config("c1"), warm=4, supercell=S)

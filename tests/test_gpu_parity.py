@@ -63,6 +63,16 @@ def test_sort_intervals(K):
     _check_one_step(_plasma((8, 12, 8), 5, vth=0.3, seed=4), sort_interval=K, warm_steps=4)
 
 
+@pytest.mark.parametrize("S", [2, 4, 8])
+def test_non_cubic_cells(S):
+    # unequal cell sizes take the kernel's general (non-cubic) instantiation
+    wl = W.uniform_plasma((16, 8, 24), 5, (0.05, 0.06, 0.045), 0.25, seed=18)
+    rng = np.random.default_rng(19)
+    wl.E = 0.3 * rng.standard_normal(wl.E.shape)
+    wl.B = 0.3 * rng.standard_normal(wl.B.shape)
+    _check_one_step(wl, supercell=S, warm_steps=3)
+
+
 def test_hot_plasma_many_crossings():
     # vth = 0.5c: a large share of particles crosses 1-3 cell faces per step
     _check_one_step(_plasma((8, 8, 8), 10, vth=0.5, seed=5), warm_steps=3)

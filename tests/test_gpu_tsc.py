@@ -65,6 +65,10 @@ def test_tsc_hot_plasma_supercells(S):
     _check(W.uniform_plasma((16, 8, 24), 6, 0.05, 0.3, seed=73), supercell=S, warm=2)
 
 
+def test_tsc_non_cubic_cells():
+    _check(W.uniform_plasma((12, 8, 16), 4, (0.05, 0.06, 0.045), 0.25, seed=80), warm=2)
+
+
 def test_tsc_random_initial_fields():
     wl = W.uniform_plasma((12, 16, 8), 5, 0.05, 0.1, seed=74)
     rng = np.random.default_rng(75)
