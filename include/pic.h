@@ -147,7 +147,9 @@ PIC_API const char* pic_last_error(const pic_ctx* ctx);
  * ux,uy,uz the momenta u^{-1/2}, w the weights; each array has n doubles.
  * Particles are given ids 0..n-1 in input order, binned by supercell and
  * stored in the library (FP64 or FP32 per `precision`).  *species_id receives
- * the species index.  Host variant: copies and returns when done. */
+ * the species index.  Host variant: copies and returns when done; page-locked
+ * host arrays (cudaHostAlloc, cudaHostRegister) are read in place by the load
+ * kernel, pageable ones are staged through device memory. */
 PIC_API int pic_add_species(pic_ctx* ctx, const pic_species_desc* s, int64_t n, const double* x, const double* y,
                     const double* z, const double* ux, const double* uy, const double* uz, const double* w,
                     int* species_id);

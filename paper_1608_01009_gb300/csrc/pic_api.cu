@@ -386,6 +386,17 @@ void free_species(Species& s) {
     s.allocs.clear();
 }
 
+// Device address of a page-locked host array (cudaHostAlloc / cudaHostRegister,
+// e.g. pinned torch tensors), or null for pageable memory.
+const double* mapped_view(const double* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<const double*>(a.devicePointer) : nullptr;
+}
+
 // (Re)allocate the store and bin tables of species s for n particles.
 int alloc_species(pic_ctx* c, Species& s, long long n) {
     cudaStreamSynchronize(c->st);
@@ -412,11 +423,14 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
         if (r) return r;
     }
     int r = PIC_OK;
-    // stage FP64 inputs on the device when they come from the host
+    // host inputs: page-locked arrays the device can address are read in place
+    // by the load kernel (over the CPU-GPU link); the others are staged
     const double* dsrc[7];
     if (!device && n > 0) {
-        if (!s.d_stage && (r = dalloc(c, s.allocs, &s.d_stage, (size_t)7 * s.cap))) return r;
         for (int k = 0; k < 7; ++k) {
+            dsrc[k] = mapped_view(src[k]);
+            if (dsrc[k]) continue;
+            if (!s.d_stage && (r = dalloc(c, s.allocs, &s.d_stage, (size_t)7 * s.cap))) return r;
             double* d = s.d_stage + (size_t)k * s.cap;
             CUDA_TRY(c, cudaMemcpyAsync(d, src[k], n * sizeof(double), cudaMemcpyHostToDevice, c->st));
             dsrc[k] = d;

@@ -108,3 +108,27 @@ def test_immobile_background_is_not_stored_and_changes_nothing():
     assert abs(b.energy()[1] - a.energy()[1]) <= 1e-12 * a.energy()[1]
     a.close()
     b.close()
+
+
+def test_pinned_host_arrays_load_like_pageable_ones():
+    # page-locked host arrays are read in place by the load kernel; pageable
+    # ones are staged: the stored particles must be identical
+    wl = W.config("c1")
+    sp = wl.species[0]
+    a = PT.make_sim(wl)
+    b = PT.make_sim(wl)
+    pinned = []
+    for arr in sp.arrays():
+        t = torch.empty(arr.shape[0], dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = arr
+        pinned.append(t)
+    b.set_particles(0, *[t.numpy() for t in pinned])
+    pa, pb = a.get_particles(0), b.get_particles(0)
+    oa, ob = np.argsort(pa["id"]), np.argsort(pb["id"])
+    for k in ("id", "x", "y", "z", "ux", "uy", "uz", "w"):
+        assert np.array_equal(pa[k][oa], pb[k][ob]), k
+    a.step(3)
+    b.step(3)
+    assert PT.rel_err(b.get_fields()[0], a.get_fields()[0]) <= 1e-13
+    a.close()
+    b.close()
