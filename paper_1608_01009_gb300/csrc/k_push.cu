@@ -247,6 +247,9 @@ __device__ __forceinline__ void deposit_by_key(R* Jt, int key, const R (&v)[12])
 #ifndef PICGB_KEYRED
 #define PICGB_KEYRED 1  // 0: segmented scan only
 #endif
+#ifndef PICGB_F32_PAIRED
+#define PICGB_F32_PAIRED 1  // FP32 kernel: packed two-wide FP32 adds in the warp scan
+#endif
 template <class R>
 struct DepositCost {
     __device__ static bool channels_win(int nruns, int rounds) {
@@ -277,6 +280,18 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
         v[4] = qy, v[5] = by, v[6] = qy * mz, v[7] = fma(by, mz, Qy * vol);
         const R qz = Qz * dz, bz = qz * mx;
         v[8] = qz, v[9] = bz, v[10] = qz * my, v[11] = fma(bz, my, Qz * vol);
+    } else if constexpr (sizeof(R) == 4 && PICGB_F32_PAIRED) {
+        // the same edge values, two at a time with packed two-wide FP32 instructions
+        const float ox = 1.0f - mx, oy = 1.0f - my, oz = 1.0f - mz;
+        const auto edges = [](float* out, float q, float qc, float o1, float m1, float o2, float m2) {
+            const float2 a = __fmul2_rn(make_float2(q, q), make_float2(o1, m1));        // (q o1, q m1)
+            const float2 lo = __ffma2_rn(a, make_float2(o2, o2), make_float2(qc, -qc));  // s2 = 0
+            const float2 hi = __ffma2_rn(a, make_float2(m2, m2), make_float2(-qc, qc));  // s2 = 1
+            out[0] = lo.x, out[1] = lo.y, out[2] = hi.x, out[3] = hi.y;
+        };
+        edges(v + 0, Qx * dx, Qx * vol, oy, my, oz, mz);
+        edges(v + 4, Qy * dy, Qy * vol, ox, mx, oz, mz);
+        edges(v + 8, Qz * dz, Qz * vol, ox, mx, oy, my);
     } else {
     const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
     {  // Jx on edges (i+1/2, j+s1, k+s2)
@@ -316,11 +331,27 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
         deposit_by_key<R, TJ, M>(Jt, key, v);
         return;
     }
-    for (int dd = 1; dd < longest; dd <<= 1) {
+    if constexpr (sizeof(R) == 4 && PICGB_F32_PAIRED) {
+        // FP32: the adds of value pairs as packed two-wide FP32 instructions
+        for (int dd = 1; dd < longest; dd <<= 1) {
+            const bool add = lane - dd >= start;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            const R t = __shfl_up_sync(FULL, v[i], dd);
-            if (lane - dd >= start) v[i] += t;
+            for (int i = 0; i < 12; i += 2) {
+                const float2 t = make_float2(__shfl_up_sync(FULL, v[i], dd), __shfl_up_sync(FULL, v[i + 1], dd));
+                if (add) {
+                    const float2 s2 = __fadd2_rn(make_float2(v[i], v[i + 1]), t);
+                    v[i] = s2.x;
+                    v[i + 1] = s2.y;
+                }
+            }
+        }
+    } else {
+        for (int dd = 1; dd < longest; dd <<= 1) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const R t = __shfl_up_sync(FULL, v[i], dd);
+                if (lane - dd >= start) v[i] += t;
+            }
         }
     }
     if (tail && key >= 0) {
