@@ -205,15 +205,15 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_add(int* __restrict__ counts, 
     }
 }
 
-// Records per lane: FP32 (36 B) eight, FP64 (64 B) two.  Each lane loads its
+// Records per lane: FP32 (36 B) eight, FP64 (64 B) four.  Each lane loads its
 // whole records before claiming their slots, so the loads overlap the slot
 // atomics (mixed 128^3 x 32 sort per step: 2 records 1.05 ms, 4 0.87 ms,
-// 8 0.84 ms).
+// 8 0.84 ms; FP64 64^3 x 50: 2 records 0.167 ms, 4 0.159 ms).
 #ifndef PICGB_SCATTER_U_F32
 #define PICGB_SCATTER_U_F32 8
 #endif
 #ifndef PICGB_SCATTER_U_F64
-#define PICGB_SCATTER_U_F64 2
+#define PICGB_SCATTER_U_F64 4
 #endif
 template <class R>
 struct ScatterU {
