@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1608_01009_gb300 import workloads as W
 from tests import parity as PT
 
@@ -71,6 +72,28 @@ def test_non_cubic_cells(S):
     wl.E = 0.3 * rng.standard_normal(wl.E.shape)
     wl.B = 0.3 * rng.standard_normal(wl.B.shape)
     _check_one_step(wl, supercell=S, warm_steps=3)
+
+
+@pytest.mark.parametrize("S", [4, 8])
+def test_largest_axis_extent(S):
+    # 1024 cells along x: the largest index the packed 10-bit cell coordinate holds
+    _check_one_step(_plasma((1024, 8, 8), 1, vth=0.3, seed=20), supercell=S, warm_steps=2)
+
+
+def test_single_relativistic_particle():
+    # one particle at gamma ~ 10 moving diagonally: crosses up to three faces per step
+    wl = _plasma((8, 8, 8), 1, vth=0.0, seed=21)
+    sp = wl.species[0]
+    keep = np.array([123])
+    for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+        setattr(sp, k, np.ascontiguousarray(getattr(sp, k)[keep]))
+    sp.ux[:] = 6.0
+    sp.uy[:] = -5.0
+    sp.uz[:] = 5.5
+    rng = np.random.default_rng(22)
+    wl.E = 0.2 * rng.standard_normal(wl.E.shape)
+    wl.B = 0.2 * rng.standard_normal(wl.B.shape)
+    _check_one_step(wl, warm_steps=5)
 
 
 def test_hot_plasma_many_crossings():
@@ -161,6 +184,25 @@ def test_absorbing_particles_leave():
     assert sim.count() < n_before
     fe = PT.field_errors(sim, ora)
     assert max(fe.values()) <= TOL, fe
+
+
+def test_every_particle_leaves():
+    # absorbing z, every particle streaming out: the store empties through the
+    # sort's compaction and the empty species keeps stepping
+    wl = _plasma((8, 8, 8), 2, vth=0.01, seed=23)
+    wl.bc = (0, 0, 1)
+    wl.absorb_cells = 2
+    sp = wl.species[0]
+    sp.uz[:] = np.where(sp.z < 0.2, -4.0, 4.0)
+    sim = PT.make_sim(wl)
+    ora = O.Oracle.from_workload(wl)
+    sim.step(40)
+    ora.step(40)
+    sim.sync()
+    assert sim.count() == 0 and int(ora.species[0].active.sum()) == 0
+    errs = PT.field_errors(sim, ora)
+    assert max(errs.values()) <= 1e-11, errs
+    sim.close()
 
 
 def test_multi_step_trajectory_c1():
