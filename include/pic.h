@@ -266,6 +266,16 @@ PIC_API int pic_tape_particle_grad(pic_ctx* ctx, int species, double* const dP[6
 PIC_API int pic_get_state(pic_ctx* ctx, void* blob, int64_t* bytes);
 PIC_API int pic_set_state(pic_ctx* ctx, const void* blob, int64_t bytes);
 
+/* Self test of the failure path of the kernels' bounded waits (a library
+ * facility; the paper has no counterpart).  A one-thread kernel arms a
+ * shared-memory barrier for a transfer that is never issued and waits on it
+ * with the particle kernel's bounded wait, limited to 10 ms of device time;
+ * the wait gives up and sets the sticky timeout flag.  Returns the status the
+ * host then reads -- PIC_ERR_TIMEOUT when the path works -- after clearing
+ * that flag, so the context stays usable; PIC_ERR_STATE if a device flag was
+ * already set before the call.  Synchronises. */
+PIC_API int pic_selftest_wait_timeout(pic_ctx* ctx);
+
 /* Field energy W_F = 1/2 dx dy dz sum (E^2 + B^2) of caller-provided fields,
  * allocating nothing.  The paper has no counterpart: this is a library
  * facility for callers that cannot allocate device memory -- a host framework

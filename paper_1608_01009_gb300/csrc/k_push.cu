@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         }
         if (!kCoef)
             for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);
-        const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT);
+        const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT, WAIT_LIMIT_NS);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
             return;

@@ -35,6 +35,7 @@ cudaError_t kinetic_launch(cudaStream_t, int, const PStore<R>&, const long long*
 cudaError_t energy_finalize_launch(cudaStream_t, const double*, int, const double*, int, double, double*);
 cudaError_t tsc_launch(int, cudaStream_t, const PushParams&, const PStore<double>&, const long long*, const double*,
                        double*, double*);
+cudaError_t wait_probe_launch(cudaStream_t, int*, uint64_t);
 
 // differentiable path (k_adjoint.cu)
 cudaError_t tape_step_launch(cudaStream_t, const TapeDev&, long long, const StepParams&, const double*, double*);
@@ -907,6 +908,28 @@ struct Cursor {
     }
 };
 
+// Every index the kernels take from a blob is checked before use: active
+// particles' cells inside the grid, chunks inside the store and the bin range.
+// (A cell far from its chunk's supercell is legal here: the particle kernel
+// flags it as outside the supercell slack and skips it.)
+bool species_payload_valid(const pic_ctx* c, const unsigned char* p, long long n, int nch) {
+    const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+    const int* cell = reinterpret_cast<const int*>(p);
+    for (long long i = 0; i < n; ++i) {
+        const int cp = cell[i];
+        if (cp >= 0 && (cell_x(cp) >= c->g.n[0] || cell_y(cp) >= c->g.n[1] || cell_z(cp) >= c->g.n[2])) return false;
+    }
+    const size_t chunk_off = pad8(n * sizeof(int)) * 2 + 7 * pad8(n * rs) + pad8(((size_t)c->g.nbins + 1) * sizeof(int));
+    const Chunk* ch = reinterpret_cast<const Chunk*>(p + chunk_off);
+    for (int k = 0; k < nch; ++k) {
+        Chunk e;
+        memcpy(&e, ch + k, sizeof e);
+        if (e.sc < 0 || e.sc >= c->g.nbins || e.start < 0 || e.count < 0 || (long long)e.start + e.count > n)
+            return false;
+    }
+    return true;
+}
+
 bool same_desc(const StateHeader& h, const pic_grid_desc& d) {
     bool ok = h.precision == d.precision && h.supercell == d.supercell && h.sort_interval == d.sort_interval &&
               (h.form_factor == 2) == (d.form_factor == 2) &&
@@ -1339,6 +1362,8 @@ int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
                 return fail(c, PIC_ERR_ARG, "bad species record in state blob");
             const size_t need = species_payload(c, sh.n, sh.nchunks);
             if (probe.left < need) return fail(c, PIC_ERR_ARG, "state blob too small");
+            if (!species_payload_valid(c, probe.p, sh.n, sh.nchunks))
+                return fail(c, PIC_ERR_ARG, "state blob holds a cell or chunk outside the grid");
             probe.p += need;
             probe.left -= need;
         }
@@ -1390,6 +1415,18 @@ int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
     c->energy_fresh = false;
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     return PIC_OK;
+}
+
+int pic_selftest_wait_timeout(pic_ctx* c) {
+    if (!c) return PIC_ERR_ARG;
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    if (device_status(c) != PIC_OK) return fail(c, PIC_ERR_STATE, "a device flag is already set");
+    CUDA_TRY(c, wait_probe_launch(c->st, c->d_err, 10000000ull));
+    c->launches += 1;
+    const int r = device_status(c);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return r;
 }
 
 int pic_tape_forward(pic_ctx* c, int nsteps, int ckpt_every, double* wk) {

@@ -141,10 +141,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Bounded wait on an mbarrier phase: returns false if `limit` polls pass
-// without completion (the caller records a timeout and leaves).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint32_t limit) {
-    uint32_t addr = smem_u32(bar);
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: returns false once `limit` polls or
+// `limit_ns` nanoseconds (whichever comes first) pass without completion; the
+// caller records a timeout and leaves.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint32_t limit,
+                                                  uint64_t limit_ns) {
+    const uint32_t addr = smem_u32(bar);
+    const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
@@ -153,6 +162,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
             : "r"(addr), "r"(phase)
             : "memory");
         if (done) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -167,9 +177,10 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// Poll budget of a TMA wait: far beyond any legitimate latency (each try_wait
-// may itself suspend for a while), short enough to return within seconds.
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+// Budget of a TMA wait: far beyond any legitimate latency (microseconds), short
+// enough that a kernel whose copy never lands returns within about a second.
+constexpr uint32_t WAIT_LIMIT = 1u << 22;         // polls (each try_wait may suspend a while)
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s of device time
 
 // ------------------------------------------------------------------ warp helpers
 // Warp-aggregated atomic add of 1 per lane on counters[key] (lanes with the

@@ -59,6 +59,7 @@ SIGNATURES = {
     "pic_species_info": [_VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32),
                          C.POINTER(C.c_int64)],
     "pic_get_state": [_VP, _VP, C.POINTER(C.c_int64)],
+    "pic_selftest_wait_timeout": [_VP],
     "pic_set_state": [_VP, _VP, C.c_int64],
     "pic_get_particles": [_VP, C.c_int, C.c_int64, C.POINTER(C.c_int64)] + [_VP] * 8,
     "pic_get_particles_dev": [_VP, C.c_int, C.c_int64, C.POINTER(C.c_int64)] + [_VP] * 8,
@@ -347,6 +348,10 @@ class Simulation:
         ptrs = (_VP * 6)(*[o.data_ptr() for o in out])
         self._check(self.lib.pic_tape_particle_grad(self.ctx, int(species), C.addressof(ptrs)))
         return dict(zip(("x", "y", "z", "ux", "uy", "uz"), out))
+
+    def selftest_wait_timeout(self) -> int:
+        """Status code of the bounded-wait failure path (PIC_ERR_TIMEOUT = -8 when it works)."""
+        return int(self.lib.pic_selftest_wait_timeout(self.ctx))
 
     def launch_count(self, reset=False) -> int:
         n = C.c_int64()

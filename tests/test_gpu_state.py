@@ -132,3 +132,51 @@ def test_pinned_host_arrays_load_like_pageable_ones():
     assert PT.rel_err(b.get_fields()[0], a.get_fields()[0]) <= 1e-13
     a.close()
     b.close()
+
+
+def test_bounded_wait_times_out_and_the_context_recovers():
+    # the particle kernel's bounded barrier wait, on a barrier nothing completes:
+    # it gives up, the host reads PIC_ERR_TIMEOUT, the context keeps working
+    wl = W.config("c1")
+    sim = PT.make_sim(wl)
+    sim.step(2)
+    assert sim.selftest_wait_timeout() == -8  # PIC_ERR_TIMEOUT
+    sim.step(2)
+    sim.sync()
+    wf, wk = sim.energy()
+    assert np.isfinite(wf) and np.isfinite(wk)
+    sim.close()
+
+
+def _cell_offset(wl):
+    """Byte offset of species 0's packed cells in a state blob of this build:
+    header (112 B), padded E|B (6 P) and J (3 P) plus the folded current
+    (3 cells) in doubles, then the 40-byte species record."""
+    P = (wl.n[0] + 4) * (wl.n[1] + 4) * (wl.n[2] + 4)
+    ncell = wl.n[0] * wl.n[1] * wl.n[2]
+    return 112 + (9 * P + 3 * ncell) * 8 + 40
+
+
+def test_particle_outside_its_supercell_slack_is_flagged():
+    # a valid cell far from its chunk's supercell: the particle kernel's own
+    # bounds check flags it (PIC_ERR_BIN_OVERFLOW) and touches no tile for it
+    wl = W.config("c1")
+    sim = PT.make_sim(wl)
+    blob = bytearray(sim.get_state())
+    off = _cell_offset(wl)
+    far = np.array([9 | (9 << 10) | (9 << 20)], dtype=np.int32).tobytes()
+    blob[off:off + 4] = far
+    sim.set_state(bytes(blob))
+    sim.step(1)
+    with pytest.raises(P.PicError) as ei:
+        sim.sync()
+    assert ei.value.code == -4  # PIC_ERR_BIN_OVERFLOW
+    sim.close()
+    # a cell outside the grid never reaches a kernel: set_state refuses it
+    sim = PT.make_sim(wl)
+    blob = bytearray(sim.get_state())
+    blob[off:off + 4] = np.array([40 | (1 << 10)], dtype=np.int32).tobytes()
+    with pytest.raises(P.PicError) as ei:
+        sim.set_state(bytes(blob))
+    assert ei.value.code == -1
+    sim.close()
