@@ -17,8 +17,10 @@
 //   * particles are read and written as coalesced SoA streams; positions are
 //     a packed global cell + an offset in the cell, so the FP64 path needs no
 //     double->int conversion (slower than an FMA on this part);
-//   * current goes to an (S+3)^3 x 3 shared-memory tile with shared atomics
-//     and is merged into the global FP64 J with one RED per non-zero node.
+//   * current goes to an (S+3)^3 shared-memory tile with shared atomics --
+//     3 edge components per cell, or for FP64 with S <= 4 the 12 moments per
+//     cell that the edge values are linear in -- and is merged into the
+//     global FP64 J with one RED per non-zero node.
 //   R = double: every value in FP64.  R = float (mixed): offsets, momenta,
 //   field tile (from the FP32 field copy), interpolation and the shared J tile
 //   in FP32; the merge into J and the kinetic-energy sum in FP64.
