@@ -11,13 +11,15 @@
 // loads and sum their currents before the shared-memory atomics):
 //   k_sort_count  : histogram of keys, warp-aggregated atomics (one atomic per
 //                   distinct key per warp); deactivated particles get no key
-//   k_scan_tiles  : per tile of SCAN_TILE keys, exclusive prefix into cursor[]
-//                   and the tile total
-//   k_scan_top    : one CTA: scan of the tile totals, new particle count, the
-//                   supercell bin starts and the chunk table the particle
-//                   kernel walks (each bin cut into near-equal chunks of at
-//                   most CHUNK particles)
-//   k_scan_add    : cursor[] += tile offset; the histogram is cleared
+//   k_scan_tiles  : per tile of SCAN_TILE keys (whole bins), exclusive prefix
+//                   into cursor[], the tile total, its bins' tile-local starts
+//                   and the number of chunks they need
+//   k_scan_top    : one CTA: scans of the per-tile particle and chunk totals,
+//                   new particle count and chunk count
+//   k_scan_add    : per tile: cursor[] += tile offset, the histogram cleared,
+//                   the bin starts made global and the tile's part of the
+//                   chunk table the particle kernel walks written (each bin cut
+//                   into near-equal chunks of at most CHUNK particles)
 //   k_sort_scatter: every active particle copied to its slot in the other
 //                   buffer (order inside a cell unspecified); deactivated
 //                   particles are dropped (compaction).  It recomputes each
@@ -109,10 +111,18 @@ __device__ int block_exclusive_scan(int v, int* s, int* total) {
     return before;
 }
 
+// Per tile of SCAN_TILE keys (whole bins: SCAN_TILE is a multiple of every
+// S^3): tile-local exclusive prefix of the counts into cursor[], the tile's
+// particle total, the tile-local start of each of its bins (into bin_start,
+// made global by k_scan_add) and the number of chunks its bins need.
 __global__ void __launch_bounds__(SCAN_NT) k_scan_tiles(const int* __restrict__ counts, long long nkeys,
-                                                       int* __restrict__ cursor, int* __restrict__ tile_sum) {
+                                                       int* __restrict__ cursor, int* __restrict__ tile_sum,
+                                                       int keys_per_bin, int* __restrict__ bin_start,
+                                                       int* __restrict__ tile_nch) {
     __shared__ int s[32];
-    const long long k0 = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_PER;
+    __shared__ int s_loc[SCAN_TILE / 8];  // tile-local bin starts (bins of >= 8 keys)
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
+    const long long k0 = base + (long long)threadIdx.x * SCAN_PER;
     int c[SCAN_PER];
     int sum = 0;
 #pragma unroll
@@ -124,83 +134,110 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_tiles(const int* __restrict__ 
     int run = block_exclusive_scan(sum, s, &total);
 #pragma unroll
     for (int i = 0; i < SCAN_PER; ++i) {
-        if (k0 + i < nkeys) cursor[k0 + i] = run;
+        const long long k = k0 + i;
+        if (k < nkeys) {
+            cursor[k] = run;
+            const int kl = (int)(k - base);
+            if (kl % keys_per_bin == 0) {
+                s_loc[kl / keys_per_bin] = run;
+                bin_start[k / keys_per_bin] = run;
+            }
+        }
         run += c[i];
     }
-    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+    __syncthreads();
+    const long long left = nkeys - base;
+    const int nb = (int)((left < SCAN_TILE ? left : SCAN_TILE) / keys_per_bin);
+    int nch = 0;
+    if ((int)threadIdx.x < nb) {
+        const int t = threadIdx.x;
+        const int cnt = (t + 1 < nb ? s_loc[t + 1] : total) - s_loc[t];
+        nch = (cnt + CHUNK - 1) / CHUNK;
+    }
+    int nch_total;
+    block_exclusive_scan(nch, s, &nch_total);
+    if (threadIdx.x == 0) {
+        tile_sum[blockIdx.x] = total;
+        tile_nch[blockIdx.x] = nch_total;
+    }
 }
 
-// One CTA: tile offsets, bin starts, chunk table, new particle count.
-__global__ void __launch_bounds__(SCAN_NT) k_scan_top(int* __restrict__ tile_sum, int ntiles,
-                                                     const int* __restrict__ cursor, long long nkeys, int keys_per_bin,
-                                                     int nbins, int* __restrict__ bin_start, long long* __restrict__ n_next,
-                                                     Chunk* __restrict__ chunks, int* __restrict__ nchunks) {
-    __shared__ int s[32];
-    __shared__ int s_total;
-    // exclusive scan of the tile totals, in place (tiles <= SCAN_NT * per)
-    const int per_t = (ntiles + SCAN_NT - 1) / SCAN_NT;
-    const int t0 = threadIdx.x * per_t, t1 = min(ntiles, t0 + per_t);
+// In-place exclusive scan of v[0..n) by one CTA; returns the total.
+__device__ int block_scan_inplace(int* v, int n, int* s) {
+    const int per = (n + SCAN_NT - 1) / SCAN_NT;
+    const int t0 = threadIdx.x * per, t1 = min(n, t0 + per);
     int sum = 0;
-    for (int t = t0; t < t1; ++t) sum += tile_sum[t];
+    for (int t = t0; t < t1; ++t) sum += v[t];
     int total;
     int run = block_exclusive_scan(sum, s, &total);
     for (int t = t0; t < t1; ++t) {
-        const int v = tile_sum[t];
-        tile_sum[t] = run;
-        run += v;
+        const int x = v[t];
+        v[t] = run;
+        run += x;
     }
-    if (threadIdx.x == 0) s_total = total;
-    __syncthreads();
-    // bin starts = key prefix at each bin's first key
-    const int per_b = (nbins + SCAN_NT - 1) / SCAN_NT;
-    const int b0 = threadIdx.x * per_b, b1 = min(nbins, b0 + per_b);
-    auto start_of = [&](int b) -> int {
-        if (b >= nbins) return s_total;
-        const long long k = (long long)b * keys_per_bin;
-        return tile_sum[k / SCAN_TILE] + cursor[k];
-    };
-    int nch = 0;
-    for (int b = b0; b < b1; ++b) {
-        const int cnt = start_of(b + 1) - start_of(b);
-        nch += (cnt + CHUNK - 1) / CHUNK;
-    }
-    int nch_total;
-    int ch = block_exclusive_scan(nch, s, &nch_total);
-    for (int b = b0; b < b1; ++b) {
-        const int st = start_of(b);
-        const int cnt = start_of(b + 1) - st;
-        bin_start[b] = st;
-        const int k = (cnt + CHUNK - 1) / CHUNK;
-        if (k > 0) {
-            const int base = cnt / k, rem = cnt % k;
-            for (int q = 0; q < k; ++q) {
-                Chunk e;
-                e.sc = b;
-                e.start = st + q * base + min(q, rem);
-                e.count = base + (q < rem ? 1 : 0);
-                e.pad = 0;
-                chunks[ch + q] = e;
-            }
-        }
-        ch += k;
-    }
+    return total;
+}
+
+// One CTA: tile particle offsets and tile chunk offsets (exclusive scans of
+// the per-tile totals), the new particle count and the chunk count.
+__global__ void __launch_bounds__(SCAN_NT) k_scan_top(int* __restrict__ tile_sum, int* __restrict__ tile_nch,
+                                                     int ntiles, int nbins, int* __restrict__ bin_start,
+                                                     long long* __restrict__ n_next, int* __restrict__ nchunks) {
+    __shared__ int s[32];
+    const int total = block_scan_inplace(tile_sum, ntiles, s);
+    const int nch_total = block_scan_inplace(tile_nch, ntiles, s);
     if (threadIdx.x == 0) {
-        bin_start[nbins] = s_total;
-        *n_next = s_total;
+        bin_start[nbins] = total;
+        *n_next = total;
         *nchunks = nch_total;
     }
 }
 
+// Per tile: cursor[] += tile offset (the histogram is cleared for the next
+// sort); the tile's bin starts made global and its bins' chunks written (each
+// bin cut into near-equal chunks of at most CHUNK particles).
 __global__ void __launch_bounds__(SCAN_NT) k_scan_add(int* __restrict__ counts, long long nkeys,
-                                                     int* __restrict__ cursor, const int* __restrict__ tile_off) {
-    const long long k0 = (long long)blockIdx.x * SCAN_TILE + threadIdx.x;
+                                                     int* __restrict__ cursor, const int* __restrict__ tile_off,
+                                                     const int* __restrict__ tile_choff, int ntiles,
+                                                     const long long* __restrict__ n_total, int keys_per_bin,
+                                                     int* __restrict__ bin_start, Chunk* __restrict__ chunks) {
+    __shared__ int s[32];
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
     const int off = tile_off[blockIdx.x];
 #pragma unroll
     for (int i = 0; i < SCAN_PER; ++i) {
-        const long long k = k0 + (long long)i * SCAN_NT;
+        const long long k = base + threadIdx.x + (long long)i * SCAN_NT;
         if (k < nkeys) {
             cursor[k] += off;
             counts[k] = 0;  // ready for the next sort
+        }
+    }
+    const long long left = nkeys - base;
+    const int nb = (int)((left < SCAN_TILE ? left : SCAN_TILE) / keys_per_bin);
+    const int b0 = (int)(base / keys_per_bin);
+    const int tile_total = (blockIdx.x + 1 < ntiles ? tile_off[blockIdx.x + 1] : (int)*n_total) - off;
+    const int t = threadIdx.x;
+    int ls = 0, cnt = 0;
+    if (t < nb) {
+        ls = bin_start[b0 + t];  // tile-local starts (k_scan_tiles); read all before any is rewritten
+        cnt = (t + 1 < nb ? bin_start[b0 + t + 1] : tile_total) - ls;
+    }
+    const int nch = (cnt + CHUNK - 1) / CHUNK;
+    int nch_total;
+    const int ch = tile_choff[blockIdx.x] + block_exclusive_scan(nch, s, &nch_total);  // (synchronises)
+    if (t < nb) {
+        const int st = off + ls;
+        bin_start[b0 + t] = st;
+        if (nch > 0) {
+            const int q0 = cnt / nch, rem = cnt % nch;
+            for (int q = 0; q < nch; ++q) {
+                Chunk e;
+                e.sc = b0 + t;
+                e.start = st + q * q0 + min(q, rem);
+                e.count = q0 + (q < rem ? 1 : 0);
+                e.pad = 0;
+                chunks[ch + q] = e;
+            }
         }
     }
 }
@@ -268,6 +305,9 @@ int sort_grid(int nsm) { return nsm * 8; }
 
 long long sort_tiles(long long nkeys) { return (nkeys + SCAN_TILE - 1) / SCAN_TILE; }
 
+// Size of the per-tile scratch (particle and chunk totals) the sort needs.
+long long sort_tile_scratch(long long nkeys) { return 2 * sort_tiles(nkeys); }
+
 template <class R>
 cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> src, PStore<R> dst,
                         const long long* n_cur, long long* n_next, int* counts, int* cursor, int* tile_sum,
@@ -275,11 +315,12 @@ cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> sr
     const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
     const int ntiles = (int)sort_tiles(nkeys);
     const int kpb = g.S * g.S * g.S;
+    int* tile_nch = tile_sum + ntiles;
     k_sort_count<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, n_cur, g, counts);
-    k_scan_tiles<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum);
-    k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, ntiles, cursor, nkeys, kpb, g.nbins, bin_start, n_next, chunks,
-                                      nchunks);
-    k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum);
+    k_scan_tiles<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, kpb, bin_start, tile_nch);
+    k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, tile_nch, ntiles, g.nbins, bin_start, n_next, nchunks);
+    k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, tile_nch, ntiles, n_next, kpb, bin_start,
+                                           chunks);
     k_sort_scatter<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, dst, n_cur, g, cursor);
     return cudaGetLastError();
 }

@@ -23,6 +23,7 @@ template <class R>
 cudaError_t sort_launch(cudaStream_t, int, const GridDev&, PStore<R>, PStore<R>, const long long*, long long*, int*,
                         int*, int*, int*, Chunk*, int*);
 long long sort_tiles(long long nkeys);
+long long sort_tile_scratch(long long nkeys);
 template <class R>
 cudaError_t load_launch(cudaStream_t, long long, const double* const*, const PStore<R>&, const GridDev&);
 template <class R>
@@ -1012,7 +1013,7 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
     if ((r = dalloc(c, c->allocs, &c->d_err, 1))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_counts, ncell))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_cursor, ncell))) return bail(r);
-    if ((r = dalloc(c, c->allocs, &c->d_tile_sum, sort_tiles(ncell)))) return bail(r);
+    if ((r = dalloc(c, c->allocs, &c->d_tile_sum, sort_tile_scratch(ncell)))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_counter, 1))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_wf, fdtd_blocks(g)))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_energy, 2))) return bail(r);
