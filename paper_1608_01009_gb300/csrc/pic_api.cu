@@ -386,6 +386,15 @@ int alloc_store(pic_ctx* c, Species& s, Store<R>& st, long long cap) {
 void free_species(Species& s) {
     for (void* p : s.allocs) cudaFree(p);
     s.allocs.clear();
+    // every device pointer of the species came from `allocs`: none may outlive it
+    // (the staging area in particular is re-allocated on first use only when null)
+    s.s64 = Store<double>{};
+    s.s32 = Store<float>{};
+    s.d_n = nullptr;
+    s.d_bin_start = nullptr;
+    s.d_chunks = nullptr;
+    s.d_nchunks = nullptr;
+    s.d_stage = nullptr;
 }
 
 // Device address of a page-locked host array (cudaHostAlloc / cudaHostRegister,

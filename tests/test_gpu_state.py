@@ -9,6 +9,8 @@
   a foreign byte string, and leaves the context usable.
 * An immobile species is stored as nothing and changes nothing: a run with
   electrons plus an immobile background equals the electron-only run.
+* A species that grows beyond its store (re-allocation) uploads whole, from
+  pinned or pageable host arrays.
 """
 import numpy as np
 import pytest
@@ -180,3 +182,25 @@ def test_particle_outside_its_supercell_slack_is_flagged():
         sim.set_state(bytes(blob))
     assert ei.value.code == -1
     sim.close()
+
+
+def test_species_grows_through_pageable_uploads():
+    # a species created from pageable host arrays, then given more particles than
+    # its store holds: the store and the host staging area are re-allocated and
+    # the upload lands whole (stored particles equal a fresh context's)
+    small = W.config("c1")
+    big = W.uniform_plasma((16, 16, 16), 20, 0.05, 0.05, seed=71)
+    assert big.nparticles > small.nparticles
+    a = PT.make_sim(small)
+    a.set_particles(0, *big.species[0].arrays())
+    b = PT.make_sim(big)
+    assert a.count(0) == b.count(0) == big.nparticles
+    pa, pb = a.get_particles(0), b.get_particles(0)
+    oa, ob = np.argsort(pa["id"]), np.argsort(pb["id"])
+    for k in ("id", "x", "y", "z", "ux", "uy", "uz", "w"):
+        assert np.array_equal(pa[k][oa], pb[k][ob]), k
+    a.step(3)
+    b.step(3)
+    assert PT.rel_err(a.get_fields()[0], b.get_fields()[0]) <= 1e-13
+    a.close()
+    b.close()
