@@ -165,6 +165,31 @@ PIC_API int pic_set_particles_dev(pic_ctx* ctx, int species, int64_t n, const do
                           const double* z, const double* ux, const double* uy, const double* uz,
                           const double* w);
 
+/* Double-buffered replacement of a species' particles, for pipelines that
+ * upload a new particle set every step.
+ *
+ * pic_upload_particles starts copying n particles (the seven arrays of
+ * pic_add_species, host or device memory) into the species' upload area on the
+ * context's copy stream and returns at once; the copy overlaps whatever the
+ * context's stream is running.  The species' current particles are untouched.
+ * Host arrays should be page-locked (copies from pageable memory complete
+ * before the call returns); the caller keeps every array unchanged until the
+ * upload has been consumed by pic_set_particles_uploaded and the context has
+ * been synchronised (pic_sync or any synchronising call).  A second upload
+ * before consumption replaces the first.  The upload area is library-owned
+ * (7 n doubles, grown on demand).  PIC_ERR_ARG: bad species, an immobile
+ * species, n out of range or a null array.
+ *
+ * pic_set_particles_uploaded replaces the species' particles with the pending
+ * upload, as pic_set_particles_dev would (ids restart at 0), ordered after the
+ * copy on the context's stream; asynchronous.  The next upload's copy waits
+ * for this load to have read the area.  PIC_ERR_STATE if no upload is
+ * pending. */
+PIC_API int pic_upload_particles(pic_ctx* ctx, int species, int64_t n, const double* x, const double* y,
+                                 const double* z, const double* ux, const double* uy, const double* uz,
+                                 const double* w);
+PIC_API int pic_set_particles_uploaded(pic_ctx* ctx, int species);
+
 /* Species properties: q, m, the immobile flag, and nid, the number of ids
  * given at the species' last load (ids run 0..nid-1; particles that left
  * through an absorbing boundary keep their ids unused).  Any output pointer

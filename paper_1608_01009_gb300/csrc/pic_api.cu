@@ -76,6 +76,13 @@ struct Species {
     int* d_nchunks = nullptr;
     double* d_ek = nullptr;        // kinetic-energy partials of the last push (push_grid entries)
     double* d_stage = nullptr;     // 7 x cap FP64 staging area for host uploads (allocated on first use)
+    // asynchronous upload (pic_upload_particles): 7 x up_cap FP64 arrays filled on
+    // the copy stream; up_n >= 0 while an upload waits to be consumed.  Not part
+    // of `allocs`: a re-allocation of the store leaves a pending upload intact.
+    double* d_up = nullptr;
+    long long up_cap = 0, up_n = -1;
+    cudaEvent_t up_done = nullptr;  // recorded on the copy stream after the copy
+    cudaEvent_t up_free = nullptr;  // recorded on the stream after the load that read the area
     long long nid = 0;             // ids 0..nid-1 were given at the last load
     std::vector<void*> allocs;
 };
@@ -123,6 +130,7 @@ struct pic_ctx {
     pic_grid_desc desc{};
     GridDev g{};
     cudaStream_t st = nullptr;
+    cudaStream_t cst = nullptr;  // copy stream of asynchronous uploads (created on first use)
     int dev = 0, nsm = 0;
     bool mixed = false;
     int K = 1, since_sort = 0;
@@ -1053,7 +1061,14 @@ int pic_destroy(pic_ctx* c) {
     if (!c) return PIC_ERR_ARG;
     cudaSetDevice(c->dev);
     cudaStreamSynchronize(c->st);
-    for (auto& s : c->sp) free_species(s);
+    if (c->cst) cudaStreamSynchronize(c->cst);
+    for (auto& s : c->sp) {
+        free_species(s);
+        if (s.d_up) cudaFree(s.d_up);
+        if (s.up_done) cudaEventDestroy(s.up_done);
+        if (s.up_free) cudaEventDestroy(s.up_free);
+    }
+    if (c->cst) cudaStreamDestroy(c->cst);
     c->tape.release();
     for (void* p : c->allocs)
         if (p) cudaFree(p);
@@ -1103,6 +1118,63 @@ int pic_set_particles_dev(pic_ctx* c, int species, int64_t n, const double* x, c
                           const double* ux, const double* uy, const double* uz, const double* w) {
     const double* src[7] = {x, y, z, ux, uy, uz, w};
     return set_particles_impl(c, species, n, src, true);
+}
+
+int pic_upload_particles(pic_ctx* c, int species, int64_t n, const double* x, const double* y, const double* z,
+                         const double* ux, const double* uy, const double* uz, const double* w) {
+    if (!c) return PIC_ERR_ARG;
+    if (species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
+    Species& s = c->sp[species];
+    if (s.immobile) return fail(c, PIC_ERR_ARG, "species %d is immobile (it stores no particles)", species);
+    if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", (long long)n);
+    const double* src[7] = {x, y, z, ux, uy, uz, w};
+    for (int k = 0; k < 7 && n > 0; ++k)
+        if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array %d", k);
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    if (!c->cst) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking));
+    if (!s.up_done) CUDA_TRY(c, cudaEventCreateWithFlags(&s.up_done, cudaEventDisableTiming));
+    if (!s.up_free) CUDA_TRY(c, cudaEventCreateWithFlags(&s.up_free, cudaEventDisableTiming));
+    if (n > s.up_cap) {
+        // grow the area once nothing reads or fills it any more
+        CUDA_TRY(c, cudaStreamSynchronize(c->cst));
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+        if (s.d_up) cudaFree(s.d_up);
+        s.d_up = nullptr;
+        s.up_cap = 0;
+        s.up_n = -1;
+        void* q = nullptr;
+        if (cudaMalloc(&q, (size_t)7 * n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PIC_ERR_OOM, "upload area of %lld particles", (long long)n);
+        }
+        s.d_up = static_cast<double*>(q);
+        s.up_cap = n;
+    }
+    // the load that consumed the previous upload must have read the area
+    CUDA_TRY(c, cudaStreamWaitEvent(c->cst, s.up_free, 0));
+    for (int k = 0; k < 7 && n > 0; ++k)
+        CUDA_TRY(c, cudaMemcpyAsync(s.d_up + (size_t)k * s.up_cap, src[k], (size_t)n * sizeof(double),
+                                    cudaMemcpyDefault, c->cst));
+    CUDA_TRY(c, cudaEventRecord(s.up_done, c->cst));
+    s.up_n = n;
+    return PIC_OK;
+}
+
+int pic_set_particles_uploaded(pic_ctx* c, int species) {
+    if (!c) return PIC_ERR_ARG;
+    if (species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species %d", species);
+    Species& s = c->sp[species];
+    if (s.up_n < 0) return fail(c, PIC_ERR_STATE, "no pending upload for species %d", species);
+    CUDA_TRY(c, cudaSetDevice(c->dev));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st, s.up_done, 0));
+    const double* src[7];
+    for (int k = 0; k < 7; ++k) src[k] = s.d_up + (size_t)k * s.up_cap;
+    const long long n = s.up_n;
+    s.up_n = -1;
+    const int r = load_particles(c, s, n, src, true);
+    // recorded even on failure, so that the next upload never waits on a stale event
+    cudaEventRecord(s.up_free, c->st);
+    return r;
 }
 
 int pic_species_info(pic_ctx* c, int species, double* q, double* m, int32_t* immobile, int64_t* nid) {

@@ -55,6 +55,8 @@ SIGNATURES = {
     "pic_add_species_dev": [_VP, C.POINTER(SpeciesDesc), C.c_int64] + [_VP] * 7 + [C.POINTER(C.c_int)],
     "pic_set_particles": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
     "pic_set_particles_dev": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
+    "pic_upload_particles": [_VP, C.c_int, C.c_int64] + [_VP] * 7,
+    "pic_set_particles_uploaded": [_VP, C.c_int],
     "pic_count_particles": [_VP, C.c_int, C.POINTER(C.c_int64)],
     "pic_species_info": [_VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32),
                          C.POINTER(C.c_int64)],
@@ -151,6 +153,7 @@ class Simulation:
         if rc != PIC_OK:
             raise PicError(rc, "pic_create failed (see stderr)")
         self.nspecies = 0
+        self._uploads = {}
 
     # ------------------------------------------------------------------ helpers
     def _check(self, rc):
@@ -159,8 +162,9 @@ class Simulation:
 
     def close(self):
         if self.ctx:
-            self.lib.pic_destroy(self.ctx)
+            self.lib.pic_destroy(self.ctx)  # waits for both streams
             self.ctx = _VP()
+        self._uploads = {}
 
     def __del__(self):
         try:
@@ -229,6 +233,26 @@ class Simulation:
         n = int(arrs[0].shape[0])
         f = self.lib.pic_set_particles_dev if dev else self.lib.pic_set_particles
         self._check(f(self.ctx, int(species), n, *[_ptr(a) for a in arrs]))
+
+    def upload_particles(self, species, x, y, z, ux, uy, uz, w):
+        """Start copying a new particle set into the species' upload area
+        (asynchronous, on the context's copy stream); set_particles_uploaded
+        installs it.  Page-locked host arrays (or device tensors) overlap the
+        copy with the running steps; the arrays must stay unchanged until the
+        upload has been installed and the context synchronised."""
+        arrs = [x, y, z, ux, uy, uz, w]
+        if _is_dev(x):
+            arrs = [a.contiguous().to(self.torch.float64) for a in arrs]
+            self.torch.cuda.current_stream().synchronize()  # the copy stream reads them next
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        n = int(arrs[0].shape[0])
+        self._uploads[int(species)] = arrs  # keep the arrays alive while the copy may run
+        self._check(self.lib.pic_upload_particles(self.ctx, int(species), n, *[_ptr(a) for a in arrs]))
+
+    def set_particles_uploaded(self, species):
+        """Replace the species' particles with the pending upload (asynchronous)."""
+        self._check(self.lib.pic_set_particles_uploaded(self.ctx, int(species)))
 
     def count(self, species=0) -> int:
         n = C.c_int64()
