@@ -94,3 +94,5 @@ def test_null_arguments(lib):
     assert lib.pic_step(None, 1) == -1
     assert lib.pic_sync(None) == -1
     assert lib.pic_last_error(None) == b"null context"
+    assert lib.pic_upload_particles(None, 0, 0, None, None, None, None, None, None, None) == -1
+    assert lib.pic_set_particles_uploaded(None, 0) == -1
