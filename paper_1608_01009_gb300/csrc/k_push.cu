@@ -151,6 +151,12 @@ __device__ __forceinline__ float below_one<float>() {
     return 0x1.fffffep-1f;
 }
 
+// min(v, largest double below 1) for v in [0, 1], on the bit pattern.
+__device__ __forceinline__ double below_one_of(double v) {
+    const long long b = __double_as_longlong(v), top = __double_as_longlong(0x1.fffffffffffffp-1);
+    return __longlong_as_double(b < top ? b : top);
+}
+
 // Crossing parameter (face - a) / d: IEEE division in FP64; in the FP32 kernel
 // the fast divide (its 2-ulp error is far below the FP32 state's own rounding).
 __device__ __forceinline__ double cross_t(double num, double d) { return num / d; }
@@ -720,9 +726,22 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     if (!act) return R(0);
 
     // ---- new cell and offset
-    const R nfx = sx ? fmin(bx - R(sx), below_one<R>()) : bx;
-    const R nfy = sy ? fmin(by - R(sy), below_one<R>()) : by;
-    const R nfz = sz ? fmin(bz - R(sz), below_one<R>()) : bz;
+    R nfx = bx, nfy = by, nfz = bz;
+    if constexpr (sizeof(R) == 8) {
+        // FP64: the shifted offsets lie in [0, 1] (non-negative, so their bit
+        // patterns order like integers) and are clamped below 1 on the integer
+        // ALU; a warp with no crossing lane skips the block (FP64-pipe issue is
+        // what bounds this kernel)
+        if (__any_sync(__activemask(), (sx | sy | sz) != 0)) {
+            if (sx) nfx = below_one_of(bx - R(sx));
+            if (sy) nfy = below_one_of(by - R(sy));
+            if (sz) nfz = below_one_of(bz - R(sz));
+        }
+    } else {
+        nfx = sx ? fmin(bx - R(sx), below_one<R>()) : bx;
+        nfy = sy ? fmin(by - R(sy), below_one<R>()) : by;
+        nfz = sz ? fmin(bz - R(sz), below_one<R>()) : bz;
+    }
     int ng[3] = {gx + sx, gy + sy, gz + sz};
     bool gone = false;
 #pragma unroll
