@@ -5,8 +5,9 @@ Bar: the FP64 path's 1e-12 per step, norm-wise per array.  Cases: one step
 from the workload's state and from a developed state (drift and sorts), a
 hot plasma with multi-face moves, random initial fields, an absorbing laser
 slab with particles leaving, several supercell sizes, ten-step
-trajectories, and the discrete charge continuity of the GPU's own current
-against TSC rho at a size the oracle only samples.
+trajectories, two species, and the discrete charge continuity of the GPU's
+own current against TSC rho at a size the oracle only samples; checkpoint
+and resume of a TSC run, and blobs of the other form factor refused.
 """
 import numpy as np
 import pytest
@@ -134,3 +135,46 @@ def test_tsc_rejects_the_tape():
         sim.tape_forward(2, 1)
     assert ei.value.code == -7  # PIC_ERR_STATE
     sim.close()
+
+
+def _two_species():
+    wl = W.uniform_plasma((12, 8, 16), 5, 0.05, 0.15, seed=91)
+    pos = W.uniform_plasma((12, 8, 16), 3, 0.05, 0.1, seed=92, q=1.0, m=1.0)
+    wl.species = wl.species + pos.species
+    return wl
+
+
+def test_tsc_two_species():
+    # electrons and positrons: both deposit into the same current, one oracle step
+    _check(_two_species(), warm=4)
+
+
+def test_tsc_checkpoint_resume_and_form_factor_mismatch():
+    wl = _two_species()
+    a = _sim(wl)
+    a.step(4)
+    blob = a.get_state()
+    a.step(5)
+    b = _sim(W.uniform_plasma((12, 8, 16), 1, 0.05, 0.0, seed=1))  # other particles
+    b.set_state(blob)
+    b.step(5)
+    for x, y in zip(a.get_fields() + (a.get_current(),), b.get_fields() + (b.get_current(),)):
+        assert PT.rel_err(y, x) <= 1e-12
+    for s in range(2):
+        pa, pb = a.get_particles(s), b.get_particles(s)
+        oa, ob = np.argsort(pa["id"]), np.argsort(pb["id"])
+        assert np.array_equal(pa["id"][oa], pb["id"][ob])
+        for k in ("x", "y", "z", "ux", "uy", "uz"):
+            assert PT.rel_err(pb[k][ob], pa[k][oa]) <= 1e-12, (s, k)
+    # a blob of the CIC form factor does not load into a TSC context, nor the reverse
+    cic = PT.make_sim(wl)
+    with pytest.raises(P.PicError) as ei:
+        cic.set_state(blob)
+    assert ei.value.code == -1
+    with pytest.raises(P.PicError) as ei:
+        b.set_state(cic.get_state())
+    assert ei.value.code == -1
+    b.step(1)
+    b.sync()
+    for s in (a, b, cic):
+        s.close()
