@@ -35,7 +35,8 @@
  *     ABI and no kernel traps; pic_last_error() gives a message;
  *   - "_dev" variants take device pointers (e.g. from torch tensors) and work
  *     asynchronously on the context's stream; the others take host pointers
- *     and return once the copy is complete;
+ *     and return once the copy is complete (except pic_upload_particles, whose
+ *     copy runs on the context's copy stream);
  *   - the caller owns every buffer it passes; the library owns its context
  *     and all device state, released by pic_destroy();
  *   - one context is used from one host thread at a time.
@@ -135,7 +136,8 @@ typedef struct pic_ctx pic_ctx;
  * field copy in mixed mode), all zero.  *out receives the context. */
 PIC_API int pic_create(const pic_grid_desc* g, pic_ctx** out);
 
-/* Wait for the context's stream and release everything it owns. */
+/* Wait for the context's stream (and its copy stream) and release everything
+ * it owns. */
 PIC_API int pic_destroy(pic_ctx* ctx);
 
 /* Message of the last error of this context ("" if none); valid until the
@@ -172,10 +174,10 @@ PIC_API int pic_set_particles_dev(pic_ctx* ctx, int species, int64_t n, const do
  * pic_add_species, host or device memory) into the species' upload area on the
  * context's copy stream and returns at once; the copy overlaps whatever the
  * context's stream is running.  The species' current particles are untouched.
- * Host arrays should be page-locked (copies from pageable memory complete
- * before the call returns); the caller keeps every array unchanged until the
- * upload has been consumed by pic_set_particles_uploaded and the context has
- * been synchronised (pic_sync or any synchronising call).  A second upload
+ * Host arrays should be page-locked (pageable arrays are read before the call
+ * returns, so their copy does not overlap).  The caller keeps every array
+ * unchanged until the upload has been consumed by pic_set_particles_uploaded
+ * and the context has been synchronised (pic_sync or any synchronising call).  A second upload
  * before consumption replaces the first.  The upload area is library-owned
  * (7 n doubles, grown on demand).  PIC_ERR_ARG: bad species, an immobile
  * species, n out of range or a null array.
