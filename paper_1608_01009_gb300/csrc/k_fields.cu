@@ -68,15 +68,20 @@ __device__ __forceinline__ double damping(const GridDev& g, int comp, bool magne
 __device__ __forceinline__ bool any_absorbing(const GridDev& g) { return (g.bc[0] | g.bc[1] | g.bc[2]) != 0; }
 
 // Store v at the cell and at its periodic ghost images (absorbing ghosts stay 0).
+// (Loops run to the fixed bound of two images, so the image lists stay in
+// registers.)
 template <class R>
 __device__ __forceinline__ void store_images(R* A, const GridDev& g, const Img& ix, const Img& iy, const Img& iz,
                                              R v) {
-    for (int c = 0; c < iz.cnt; ++c) {
-        if (!iz.fold[c]) continue;
-        for (int b = 0; b < iy.cnt; ++b) {
-            if (!iy.fold[b]) continue;
-            for (int a = 0; a < ix.cnt; ++a) {
-                if (!ix.fold[a]) continue;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (c >= iz.cnt || !iz.fold[c]) continue;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (b >= iy.cnt || !iy.fold[b]) continue;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (a >= ix.cnt || !ix.fold[a]) continue;
                 A[pidx(g, ix.idx[a], iy.idx[b], iz.idx[c])] = v;
             }
         }
@@ -96,7 +101,14 @@ __device__ __forceinline__ bool cell_of_thread(const GridDev& g, int& i, int& j,
 
 __device__ __forceinline__ int flat_block() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
-__global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, GridDev g, double h, int last,
+// hr[a] = h / d_a and dtr[a] = dt / d_a come from the host: each component's
+// update is then two differences and two (B) or three (E) fused multiply-adds,
+// FP64-pipe issue being what these kernels spend most.
+struct Fac3 {
+    double v[3];
+};
+
+__global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, GridDev g, Fac3 hr, int last,
                                                     float* __restrict__ EB32, double* __restrict__ wf_part) {
     __shared__ double red[FDTD_NT / 32];
     double e2 = 0.0;
@@ -108,12 +120,12 @@ __global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, Gri
         const double* Ey = EB + g.P;
         const double* Ez = EB + 2 * g.P;
         double* B = EB + 3 * g.P;
-        const double rx = g.rd[0], ry = g.rd[1], rz = g.rd[2];
+        const double hx = hr.v[0], hy = hr.v[1], hz = hr.v[2];
         const double ex = Ex[o], ey = Ey[o], ez = Ez[o];
-        const double cx = (Ez[o + sy] - ez) * ry - (Ey[o + sz] - ey) * rz;
-        const double cy = (Ex[o + sz] - ex) * rz - (Ez[o + 1] - ez) * rx;
-        const double cz = (Ey[o + 1] - ey) * rx - (Ex[o + sy] - ex) * ry;
-        double b[3] = {B[o] - h * cx, B[g.P + o] - h * cy, B[2 * g.P + o] - h * cz};
+        // B - h curl E, curl E = (dy Ez - dz Ey, dz Ex - dx Ez, dx Ey - dy Ex) by forward differences
+        double b[3] = {fma(-hy, Ez[o + sy] - ez, fma(hz, Ey[o + sz] - ey, B[o])),
+                       fma(-hz, Ex[o + sz] - ex, fma(hx, Ez[o + 1] - ez, B[g.P + o])),
+                       fma(-hx, Ey[o + 1] - ey, fma(hy, Ex[o + sy] - ex, B[2 * g.P + o]))};
         if (any_absorbing(g))
             for (int c = 0; c < 3; ++c) b[c] *= damping(g, c, true, i, j, k);
         const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
@@ -136,7 +148,7 @@ __global__ void __launch_bounds__(FDTD_NT) k_fdtd_b(double* __restrict__ EB, Gri
 }
 
 __global__ void __launch_bounds__(FDTD_NT) k_fdtd_e(double* __restrict__ EB, double* __restrict__ J,
-                                                    double* __restrict__ Jlast, GridDev g) {
+                                                    double* __restrict__ Jlast, GridDev g, Fac3 dtr) {
     const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
     int i, j, k;
     if (!cell_of_thread(g, i, j, k)) return;
@@ -155,10 +167,13 @@ __global__ void __launch_bounds__(FDTD_NT) k_fdtd_e(double* __restrict__ EB, dou
     const Img ix = images(i, g.n[0], g.bc[0]), iy = images(j, g.n[1], g.bc[1]), iz = images(k, g.n[2], g.bc[2]);
     if (ix.cnt * iy.cnt * iz.cnt > 1) {
         // boundary cell: add the periodic ghost images of J, zero every image read
-        for (int c3 = 0; c3 < iz.cnt; ++c3)
-            for (int b3 = 0; b3 < iy.cnt; ++b3)
-                for (int a3 = 0; a3 < ix.cnt; ++a3) {
-                    if ((a3 | b3 | c3) == 0) continue;
+#pragma unroll
+        for (int c3 = 0; c3 < 2; ++c3)
+#pragma unroll
+            for (int b3 = 0; b3 < 2; ++b3)
+#pragma unroll
+                for (int a3 = 0; a3 < 2; ++a3) {
+                    if (c3 >= iz.cnt || b3 >= iy.cnt || a3 >= ix.cnt || (a3 | b3 | c3) == 0) continue;
                     const long long q = pidx(g, ix.idx[a3], iy.idx[b3], iz.idx[c3]);
                     const bool fold = ix.fold[a3] && iy.fold[b3] && iz.fold[c3];
                     for (int c = 0; c < 3; ++c) {
@@ -171,11 +186,11 @@ __global__ void __launch_bounds__(FDTD_NT) k_fdtd_e(double* __restrict__ EB, dou
         J[c * g.P + o] = 0.0;
         Jlast[c * ncell + t] = jc[c];
     }
-    const double rx = g.rd[0], ry = g.rd[1], rz = g.rd[2];
-    const double cx = (bz - bz_y) * ry - (by - by_z) * rz;
-    const double cy = (bx - bx_z) * rz - (bz - bz_x) * rx;
-    const double cz = (by - by_x) * rx - (bx - bx_y) * ry;
-    double e[3] = {e0 + g.dt * (cx - jc[0]), e1 + g.dt * (cy - jc[1]), e2 + g.dt * (cz - jc[2])};
+    // E + dt (curl B - J), curl B by backward differences
+    const double tx = dtr.v[0], ty = dtr.v[1], tz = dtr.v[2], dt = g.dt;
+    double e[3] = {fma(ty, bz - bz_y, fma(-tz, by - by_z, fma(-dt, jc[0], e0))),
+                   fma(tz, bx - bx_z, fma(-tx, bz - bz_x, fma(-dt, jc[1], e1))),
+                   fma(tx, by - by_x, fma(-ty, bx - bx_y, fma(-dt, jc[2], e2)))};
     if (any_absorbing(g))
         for (int c = 0; c < 3; ++c) e[c] *= damping(g, c, false, i, j, k);
     for (int c = 0; c < 3; ++c) store_images(EB + c * g.P, g, ix, iy, iz, e[c]);
@@ -222,12 +237,14 @@ int fdtd_blocks(const GridDev& g) {
 
 cudaError_t fdtd_b_launch(cudaStream_t st, double* EB, const GridDev& g, double h, int last, float* EB32,
                           double* wf_part) {
-    k_fdtd_b<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, g, h, last, EB32, wf_part);
+    const Fac3 hr{{h * g.rd[0], h * g.rd[1], h * g.rd[2]}};
+    k_fdtd_b<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, g, hr, last, EB32, wf_part);
     return cudaGetLastError();
 }
 
 cudaError_t fdtd_e_launch(cudaStream_t st, double* EB, double* J, double* Jlast, const GridDev& g) {
-    k_fdtd_e<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, J, Jlast, g);
+    const Fac3 dtr{{g.dt * g.rd[0], g.dt * g.rd[1], g.dt * g.rd[2]}};
+    k_fdtd_e<<<fdtd_grid(g), dim3(FDTD_BX, FDTD_BY), 0, st>>>(EB, J, Jlast, g, dtr);
     return cudaGetLastError();
 }
 
