@@ -45,6 +45,9 @@ MUTATIONS = [
      "dS[a][2] = T(-1.0) * d[a] * (delta0 - delta1);"),
     ("TSC rho weight", "sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][c])",
      "sp->q * sp->w[p] / dV * (w[0][a] * w[1][b] * w[2][b])"),
+    ("damping staggering", "double off = isB ? stagB(c, a) : stagE(c, a);",
+     "double off = isB ? stagE(c, a) : stagB(c, a);"),
+    ("damping distance", "double dist = std::min(p, (double)n - p);", "double dist = std::min(p, (double)n - 1 - p);"),
 ]
 
 

@@ -15,7 +15,8 @@ it is itself checked here against results the method and the mathematics fix
                the discrete vacuum energy invariant;
 * whole step-- constancy of the Gauss-law residual div E - rho; a brute-force
                step-by-step restatement on a few particles;
-* absorbing -- a pulse entering the damping layer loses its energy; particles
+* absorbing -- the damping factor at every staggered lattice point of the layer;
+               a pulse entering the damping layer loses its energy; particles
                leaving the domain are deactivated.
 """
 import math
@@ -369,6 +370,34 @@ def test_absorbing_layer_removes_pulse():
     for _ in range(240):
         _vacuum_steps(ora, 1)
     assert ora.field_energy() < 0.05 * w0
+
+
+def test_absorbing_damping_profile():
+    # The layer is a reading (the paper has none): after each field sub-update a
+    # component is multiplied by 1 - sigma ((L - dist)/L)^2 inside L cells, dist
+    # the distance in cells of the component's own lattice point from the nearer
+    # boundary.  With E = 0 the B half step is that factor alone, with B = 0 and
+    # J = 0 so is the E update; the x offsets are the Yee staggering (Bx at i,
+    # By and Bz at i + 1/2; Ex at i + 1/2, Ey and Ez at i).
+    n, d, L, sigma = (24, 4, 4), (0.1, 0.1, 0.1), 8, 0.1
+    shape = (3, n[2], n[1], n[0])
+    p = np.arange(n[0], dtype=float)
+
+    def factor(off):
+        dist = np.minimum(p + off, n[0] - (p + off))
+        return np.where(dist < L, 1.0 - sigma * ((L - dist) / L) ** 2, 1.0)
+
+    ora = O.Oracle(n, d, 0.01, bc=(1, 0, 0), absorb_cells=L, absorb_sigma=sigma, E=np.zeros(shape),
+                   B=np.ones(shape))
+    ora.fdtd_b_half()
+    for c, off in enumerate((0.0, 0.5, 0.5)):
+        assert np.max(np.abs(ora.B[c] - factor(off)[None, None, :])) < 1e-15, c
+    ora = O.Oracle(n, d, 0.01, bc=(1, 0, 0), absorb_cells=L, absorb_sigma=sigma, E=np.ones(shape),
+                   B=np.zeros(shape))
+    ora.fdtd_e()
+    for c, off in enumerate((0.5, 0.0, 0.0)):
+        assert np.max(np.abs(ora.E[c] - factor(off)[None, None, :])) < 1e-15, c
+    assert abs(factor(0.0)[0] - 0.9) < 1e-15  # the boundary itself: 1 - sigma
 
 
 def test_absorbing_deactivates_leaving_particles():
