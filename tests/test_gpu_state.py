@@ -151,7 +151,7 @@ def test_bounded_wait_times_out_and_the_context_recovers():
 
 
 def _cell_offset(wl):
-    """Byte offset of species 0's packed cells in a state blob of this build:
+    """Byte offset of species 0's packed cells in a state blob of the current format:
     header (112 B), padded E|B (6 P) and J (3 P) plus the folded current
     (3 cells) in doubles, then the 40-byte species record."""
     P = (wl.n[0] + 4) * (wl.n[1] + 4) * (wl.n[2] + 4)
