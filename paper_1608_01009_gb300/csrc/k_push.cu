@@ -653,8 +653,10 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
             int base = 0;
             if (lane == first) base = atomicAdd(s_qn, __popc(cm));
             base = __shfl_sync(FULL, base, first);
-            if (cross) {
-                const int q = qbase + base + __popc(cm & ((1u << lane) - 1u));
+            const int slot = base + __popc(cm & ((1u << lane) - 1u));
+            if (cross && slot >= CHUNK) atomicOr(err, ERRBIT_DRIFT);  // a chunk longer than CHUNK: dropped
+            if (cross && slot < CHUNK) {
+                const int q = qbase + slot;
                 xq.key[q] = key0;
                 xq.a[0][q] = fx;
                 xq.a[1][q] = fy;
@@ -825,7 +827,10 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
             for (int i = threadIdx.x; i < 3 * TJ3; i += NT) Jt[i] = R(0);
         const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT, WAIT_LIMIT_NS);
         if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+            if (threadIdx.x == 0) {
+                atomicOr(err, ERRBIT_TIMEOUT);
+                ek_part[blockIdx.x] = 0.0;  // no stale partial of an earlier launch survives
+            }
             return;
         }
         phase ^= 1u;
@@ -855,7 +860,7 @@ __global__ void __launch_bounds__(NT, push_min_blocks<R>()) k_push(const __grid_
         ek += (double)ek_chunk;
         __syncthreads();
         // the deferred crossing moves (FP64), split by every thread of the CTA
-        const int nq = sizeof(R) == 8 ? s_qn : 0;
+        const int nq = sizeof(R) == 8 ? min(s_qn, CHUNK) : 0;
         for (int i = threadIdx.x; i < nq; i += NT) {
             const int q = qbase + i;
             const R w = xq.w[q];

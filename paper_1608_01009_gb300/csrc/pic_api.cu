@@ -429,6 +429,8 @@ int alloc_species(pic_ctx* c, Species& s, long long n) {
     if (!r) r = c->mixed ? alloc_store(c, s, s.s32, cap) : alloc_store(c, s, s.s64, cap);
     if (r) return r;
     CUDA_TRY(c, cudaMemsetAsync(s.d_nchunks, 0, sizeof(int), c->st));
+    // an immobile species is never sorted: its (empty) bins stay at 0
+    CUDA_TRY(c, cudaMemsetAsync(s.d_bin_start, 0, ((size_t)c->g.nbins + 1) * sizeof(int), c->st));
     return PIC_OK;
 }
 
@@ -882,13 +884,16 @@ int tape_backward_impl(pic_ctx* c, double wk_weight, const double* const gE[3], 
 // ---------------------------------------------------------------- state blob
 namespace {
 
-const char STATE_MAGIC[8] = {'P', 'I', 'C', 'G', 'B', 'S', 'T', '1'};
+const char STATE_MAGIC[8] = {'P', 'I', 'C', 'G', 'B', 'S', 'T', '2'};
 
+// chunk: the build's CHUNK (most particles of one chunk), which bounds every
+// chunk of the blob's table and the particle kernel's per-CTA queue slots.
 struct StateHeader {
     char magic[8];
     int32_t precision, supercell, sort_interval, absorb_cells;
     int32_t n[3], bc[3];
     int32_t nspecies, form_factor;
+    int32_t chunk, reserved;
     double d[3], dt, absorb_sigma;
     int64_t steps, since_sort;
 };
@@ -927,9 +932,11 @@ struct Cursor {
 };
 
 // Every index the kernels take from a blob is checked before use: active
-// particles' cells inside the grid, chunks inside the store and the bin range.
-// (A cell far from its chunk's supercell is legal here: the particle kernel
-// flags it as outside the supercell slack and skips it.)
+// particles' cells inside the grid; bin starts non-decreasing from 0 to n;
+// every chunk inside its own bin's range and at most CHUNK particles long
+// (the particle kernel gives each particle of a chunk one of CHUNK per-CTA
+// queue slots).  A cell far from its chunk's supercell is legal here: the
+// particle kernel flags it as outside the supercell slack and skips it.
 bool species_payload_valid(const pic_ctx* c, const unsigned char* p, long long n, int nch) {
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
     const int* cell = reinterpret_cast<const int*>(p);
@@ -937,19 +944,33 @@ bool species_payload_valid(const pic_ctx* c, const unsigned char* p, long long n
         const int cp = cell[i];
         if (cp >= 0 && (cell_x(cp) >= c->g.n[0] || cell_y(cp) >= c->g.n[1] || cell_z(cp) >= c->g.n[2])) return false;
     }
-    const size_t chunk_off = pad8(n * sizeof(int)) * 2 + 7 * pad8(n * rs) + pad8(((size_t)c->g.nbins + 1) * sizeof(int));
+    const size_t bin_off = pad8(n * sizeof(int)) * 2 + 7 * pad8(n * rs);
+    const int* bs = reinterpret_cast<const int*>(p + bin_off);
+    const int nb = c->g.nbins;
+    for (int b = 0; b <= nb; ++b) {
+        int v, prev = 0;
+        memcpy(&v, bs + b, sizeof v);
+        if (b > 0) memcpy(&prev, bs + b - 1, sizeof prev);
+        if (v < prev || v > n || (b == 0 && v != 0) || (b == nb && v != n)) return false;
+    }
+    const size_t chunk_off = bin_off + pad8(((size_t)nb + 1) * sizeof(int));
     const Chunk* ch = reinterpret_cast<const Chunk*>(p + chunk_off);
     for (int k = 0; k < nch; ++k) {
         Chunk e;
         memcpy(&e, ch + k, sizeof e);
-        if (e.sc < 0 || e.sc >= c->g.nbins || e.start < 0 || e.count < 0 || (long long)e.start + e.count > n)
+        if (e.sc < 0 || e.sc >= nb || e.start < 0 || e.count < 0 || e.count > CHUNK ||
+            (long long)e.start + e.count > n)
             return false;
+        int b0, b1;
+        memcpy(&b0, bs + e.sc, sizeof b0);
+        memcpy(&b1, bs + e.sc + 1, sizeof b1);
+        if (e.start < b0 || e.start + e.count > b1) return false;
     }
     return true;
 }
 
 bool same_desc(const StateHeader& h, const pic_grid_desc& d) {
-    bool ok = h.precision == d.precision && h.supercell == d.supercell && h.sort_interval == d.sort_interval &&
+    bool ok = h.chunk == CHUNK && h.precision == d.precision && h.supercell == d.supercell && h.sort_interval == d.sort_interval &&
               (h.form_factor == 2) == (d.form_factor == 2) &&
               h.absorb_cells == d.absorb_cells && h.dt == d.dt && h.absorb_sigma == d.absorb_sigma;
     for (int a = 0; a < 3; ++a) ok = ok && h.n[a] == d.n[a] && h.bc[a] == d.bc[a] && h.d[a] == d.d[a];
@@ -1384,6 +1405,7 @@ int pic_get_state(pic_ctx* c, void* blob, int64_t* bytes) {
     h.absorb_sigma = c->desc.absorb_sigma;
     h.nspecies = (int32_t)c->sp.size();
     h.form_factor = c->desc.form_factor == 2 ? 2 : 1;
+    h.chunk = CHUNK;
     h.steps = c->steps;
     h.since_sort = c->since_sort;
     memcpy(at, &h, sizeof h);
@@ -1426,6 +1448,10 @@ int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
     if (memcmp(h.magic, STATE_MAGIC, 8) != 0) return fail(c, PIC_ERR_ARG, "not a state blob of this library");
     if (!same_desc(h, c->desc)) return fail(c, PIC_ERR_ARG, "state blob was written for another grid descriptor");
     if (h.nspecies < 0 || h.nspecies > MAX_SPECIES) return fail(c, PIC_ERR_ARG, "bad species count in state blob");
+    // steps since the last sort: a larger value would delay the next sort past the
+    // supercell slack the particle kernel's tile allows
+    if (h.since_sort < 0 || h.since_sort > c->K || h.steps < 0)
+        return fail(c, PIC_ERR_ARG, "bad step counters in state blob");
     if (cur.left < grid_payload(c)) return fail(c, PIC_ERR_ARG, "state blob too small");
     // validate every species section before touching the context
     {

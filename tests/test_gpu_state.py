@@ -150,13 +150,67 @@ def test_bounded_wait_times_out_and_the_context_recovers():
     sim.close()
 
 
+HEADER = 120  # state blob header bytes (the since_sort counter is its last 8)
+
+
 def _cell_offset(wl):
     """Byte offset of species 0's packed cells in a state blob of the current format:
-    header (112 B), padded E|B (6 P) and J (3 P) plus the folded current
+    header (120 B), padded E|B (6 P) and J (3 P) plus the folded current
     (3 cells) in doubles, then the 40-byte species record."""
     P = (wl.n[0] + 4) * (wl.n[1] + 4) * (wl.n[2] + 4)
     ncell = wl.n[0] * wl.n[1] * wl.n[2]
-    return 112 + (9 * P + 3 * ncell) * 8 + 40
+    return HEADER + (9 * P + 3 * ncell) * 8 + 40
+
+
+def _pad8(x):
+    return (x + 7) & ~7
+
+
+def _chunk_table(blob, wl, n, nbins, real=8):
+    """Offsets of species 0's bin starts and chunk table, and the chunk count
+    (from the species record), in a state blob of the current format."""
+    cells = _cell_offset(wl)
+    nch = int(np.frombuffer(bytes(blob[cells - 4:cells]), dtype=np.int32)[0])
+    bins = cells + 2 * _pad8(4 * n) + 7 * _pad8(real * n)
+    return bins, bins + _pad8(4 * (nbins + 1)), nch
+
+
+def test_set_state_bounds_every_chunk_and_the_sort_counter():
+    # a chunk longer than CHUNK (the particle kernel's per-CTA queue slots), a
+    # chunk that leaves its bin, and a since-sort counter beyond the sort
+    # interval are refused before any kernel sees them
+    wl = W.uniform_plasma((8, 8, 8), 100, 0.05, 0.05, seed=63)  # 6400 particles per 4^3 bin
+    sim = PT.make_sim(wl)
+    good = bytearray(sim.get_state())
+    n, nbins = wl.nparticles, 8
+    bins, chunks, nch = _chunk_table(good, wl, n, nbins)
+    table = np.frombuffer(bytes(good[chunks:chunks + 16 * nch]), dtype=np.int32).reshape(nch, 4).copy()
+    starts = np.frombuffer(bytes(good[bins:bins + 4 * (nbins + 1)]), dtype=np.int32)
+    assert nch == 2 * nbins and table[0, 0] == table[1, 0] == 0  # bin 0 cut into two chunks
+    assert table[0, 2] + table[1, 2] == starts[1] - starts[0] > 4096
+    bad = bytearray(good)  # bin 0 as one chunk of 6400 particles
+    t = table.copy()
+    t[0, 2] = starts[1] - starts[0]
+    bad[chunks:chunks + 16 * nch] = t.tobytes()
+    with pytest.raises(P.PicError) as ei:
+        sim.set_state(bytes(bad))
+    assert ei.value.code == -1
+    bad = bytearray(good)  # a chunk of bin 0 that runs into bin 1
+    t = table.copy()
+    t[1, 2] += 1
+    bad[chunks:chunks + 16 * nch] = t.tobytes()
+    with pytest.raises(P.PicError) as ei:
+        sim.set_state(bytes(bad))
+    assert ei.value.code == -1
+    bad = bytearray(good)  # steps since the last sort beyond the sort interval
+    bad[HEADER - 8:HEADER] = np.array([1000], dtype=np.int64).tobytes()
+    with pytest.raises(P.PicError) as ei:
+        sim.set_state(bytes(bad))
+    assert ei.value.code == -1
+    sim.set_state(bytes(good))  # the context is still usable
+    sim.step(2)
+    sim.sync()
+    sim.close()
 
 
 def test_particle_outside_its_supercell_slack_is_flagged():
