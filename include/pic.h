@@ -131,17 +131,19 @@ typedef struct {
 
 typedef struct pic_ctx pic_ctx;
 
-/* Create a context: validates `g` (PIC_ERR_ARG, PIC_ERR_CFL) before touching
- * the GPU, then allocates the ghost-padded FP64 E, B, J grids (and the FP32
- * field copy in mixed mode), all zero.  *out receives the context. */
+/* Create a context (Sec. 2: the field and the current density are defined on
+ * a discrete grid, on which Maxwell's equations are integrated): validates
+ * `g` (PIC_ERR_ARG, PIC_ERR_CFL) before touching the GPU, then allocates the
+ * ghost-padded FP64 E, B, J grids (and the FP32 field copy in mixed mode), all
+ * zero.  *out receives the context. */
 PIC_API int pic_create(const pic_grid_desc* g, pic_ctx** out);
 
 /* Wait for the context's stream (and its copy stream) and release everything
- * it owns. */
+ * it owns (a library facility; the paper has no counterpart). */
 PIC_API int pic_destroy(pic_ctx* ctx);
 
 /* Message of the last error of this context ("" if none); valid until the
- * next call on the context. */
+ * next call on the context (a library facility). */
 PIC_API const char* pic_last_error(const pic_ctx* ctx);
 
 /* Add a species of n macro-particles (Sec. 2: the plasma is represented by
@@ -159,8 +161,9 @@ PIC_API int pic_add_species_dev(pic_ctx* ctx, const pic_species_desc* s, int64_t
                         const double* y, const double* z, const double* ux, const double* uy,
                         const double* uz, const double* w, int* species_id);
 
-/* Replace all particles of an existing species (same layout as
- * pic_add_species; ids restart at 0).  Used to load a new state. */
+/* Replace all particles of an existing species (Sec. 2: the macro-particle
+ * ensemble; same layout as pic_add_species; ids restart at 0).  Used to load
+ * a new state. */
 PIC_API int pic_set_particles(pic_ctx* ctx, int species, int64_t n, const double* x, const double* y, const double* z,
                       const double* ux, const double* uy, const double* uz, const double* w);
 PIC_API int pic_set_particles_dev(pic_ctx* ctx, int species, int64_t n, const double* x, const double* y,
@@ -168,7 +171,8 @@ PIC_API int pic_set_particles_dev(pic_ctx* ctx, int species, int64_t n, const do
                           const double* w);
 
 /* Double-buffered replacement of a species' particles, for pipelines that
- * upload a new particle set every step.
+ * upload a new particle set every step (a library facility around the
+ * macro-particle ensemble of Sec. 2).
  *
  * pic_upload_particles starts copying n particles (the seven arrays of
  * pic_add_species, host or device memory) into the species' upload area on the
@@ -192,16 +196,19 @@ PIC_API int pic_upload_particles(pic_ctx* ctx, int species, int64_t n, const dou
                                  const double* w);
 PIC_API int pic_set_particles_uploaded(pic_ctx* ctx, int species);
 
-/* Species properties: q, m, the immobile flag, and nid, the number of ids
- * given at the species' last load (ids run 0..nid-1; particles that left
+/* Species properties (Sec. 2: each macro-particle species has its charge and
+ * mass): q, m, the immobile flag, and nid, the number of ids given at the
+ * species' last load (ids run 0..nid-1; particles that left
  * through an absorbing boundary keep their ids unused).  Any output pointer
  * may be NULL. */
 PIC_API int pic_species_info(pic_ctx* ctx, int species, double* q, double* m, int32_t* immobile, int64_t* nid);
 
-/* Number of active particles of a species (synchronises the stream). */
+/* Number of active particles of a species (Sec. 2; particles that left
+ * through an absorbing boundary are not counted).  Synchronises the stream. */
 PIC_API int pic_count_particles(pic_ctx* ctx, int species, int64_t* n);
 
-/* Copy out the active particles of a species: ids, physical positions
+/* Copy out the active particles of a species (the macro-particle state of
+ * Sec. 2 that the step advances): ids, physical positions
  * (wrapped into the domain on periodic axes), momenta and weights, FP64.
  * Order is the library's internal (binned) order; match by id.  `cap` is
  * the length of the caller's arrays; *n receives the count written
@@ -211,42 +218,50 @@ PIC_API int pic_get_particles(pic_ctx* ctx, int species, int64_t cap, int64_t* n
 PIC_API int pic_get_particles_dev(pic_ctx* ctx, int species, int64_t cap, int64_t* n, int64_t* id, double* x,
                           double* y, double* z, double* ux, double* uy, double* uz, double* w);
 
-/* Set / get E and B (unpadded layout above; E[c], B[c] one array per
- * component).  Setting refreshes the periodic ghost layers and the FP32
- * copy.  Getting returns E^n, B^n of the current state. */
+/* Set / get E and B, the grid fields of Sec. 2 (unpadded layout above; E[c],
+ * B[c] one array per component).  Setting refreshes the periodic ghost layers
+ * and the FP32 copy.  Getting returns E^n, B^n of the current state. */
 PIC_API int pic_set_fields(pic_ctx* ctx, const double* const E[3], const double* const B[3]);
 PIC_API int pic_set_fields_dev(pic_ctx* ctx, const double* const E[3], const double* const B[3]);
 PIC_API int pic_get_fields(pic_ctx* ctx, double* const E[3], double* const B[3]);
 PIC_API int pic_get_fields_dev(pic_ctx* ctx, double* const E[3], double* const B[3]);
 
-/* The current density J^{n+1/2} deposited by the last step (periodic images
- * folded onto their owners), same layout as E. */
+/* The current density J^{n+1/2} deposited by the last step (Sec. 2: the
+ * current computed from the particles feeds Maxwell's equations; Sec. 3: the
+ * Villasenor-Buneman scheme), periodic images folded onto their owners, same
+ * layout as E. */
 PIC_API int pic_get_current(pic_ctx* ctx, double* const J[3]);
 PIC_API int pic_get_current_dev(pic_ctx* ctx, double* const J[3]);
 
-/* Advance nsteps whole steps (the order above), asynchronously on the
- * stream.  Every `sort_interval` steps the particles are re-binned by
+/* Advance nsteps whole steps (the stages of Sec. 2 in the order above: field
+ * interpolation, equations of motion, current deposition, field update; with
+ * the schemes of Sec. 3), asynchronously on the stream.  Particles are
+ * processed by supercells (Sec. 4.3).  Every `sort_interval` steps the particles are re-binned by
  * supercell (an on-device counting sort).  Device-side faults are recorded in
  * a sticky flag that pic_sync() returns. */
 PIC_API int pic_step(pic_ctx* ctx, int nsteps);
 
 /* Wait for the stream; return the sticky device status (PIC_OK,
- * PIC_ERR_BIN_OVERFLOW, PIC_ERR_TIMEOUT, PIC_ERR_NAN) or PIC_ERR_CUDA. */
+ * PIC_ERR_BIN_OVERFLOW, PIC_ERR_TIMEOUT, PIC_ERR_NAN) or PIC_ERR_CUDA (a
+ * library facility). */
 PIC_API int pic_sync(pic_ctx* ctx);
 
-/* Energy of the current state (synchronises): field energy
+/* Energy of the current state (a diagnostic; the paper reports none, its
+ * runs measure time only).  Synchronises.  Field energy
  * W_F = 1/2 dV sum (E^2 + B^2) and kinetic energy W_K = sum m w (gamma - 1)
  * over active particles, gamma from the stored u^{n-1/2}; FP64. */
 PIC_API int pic_energy(pic_ctx* ctx, double* wf, double* wk);
 
 /* Turn per-stage CUDA-event timing on (1) or off (0, the default), and read
- * the accumulated milliseconds: out[0] particle push + current deposition
+ * the accumulated milliseconds (the stage split of the paper's Table 6: push,
+ * deposit, other): out[0] particle push + current deposition
  * (one fused kernel per species), out[1] field solver, out[2] supercell sort,
  * out[3] diagnostics.  pic_stage_times synchronises. */
 PIC_API int pic_enable_timing(pic_ctx* ctx, int on);
 PIC_API int pic_stage_times(pic_ctx* ctx, double out[4]);
 
-/* Kernels this context has launched since creation (or the last reset). */
+/* Kernels this context has launched since creation (or the last reset); a
+ * library facility. */
 PIC_API int pic_launch_count(pic_ctx* ctx, int64_t* n, int reset);
 
 /* Differentiable runs: a hand-written discrete adjoint of the whole step
@@ -326,6 +341,18 @@ PIC_API int pic_selftest_wait_timeout(pic_ctx* ctx);
  * PIC_ERR_CUDA. */
 PIC_API int pic_field_energy_noalloc(const double* const E[3], const double* const B[3], const int32_t n[3],
                                      const double d[3], double* wf, void* stream);
+
+/* Measured FP64 fused multiply-add throughput of a device, the denominator
+ * of the FP64 particle kernel's roofline (a library facility for
+ * measurement; the paper has no counterpart).  It needs no context and
+ * allocates nothing.  A kernel of independent FMA chains
+ * (4 CTAs of 256 threads per SM, 8 chains per thread, `iters` FMAs per chain)
+ * runs once untimed and three times timed on a private stream of `device`;
+ * *tflops receives 2 x FMAs / the fastest timed launch in TFLOP/s and *ms
+ * that launch's milliseconds.  iters in 1..2^30 (2048 takes a few ms on a
+ * GB300).  Synchronises.  PIC_ERR_ARG for a null output or iters out of
+ * range, PIC_ERR_CUDA if the device or a launch fails. */
+PIC_API int pic_probe_fp64_fma(int device, int64_t iters, double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

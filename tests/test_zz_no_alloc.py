@@ -33,7 +33,7 @@ def _noalloc(lib, E, B, n, d, out, stream):
                                         C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
 
 
-def test_noalloc_field_energy_matches_pic_energy_twice(lib):
+def test_noalloc_field_energy_matches_pic_energy_and_numpy_twice(lib):
     from paper_1608_01009_gb300 import pic as P
     n, d = (24, 16, 20), (0.05, 0.06, 0.04)
     sim = P.Simulation(n, d, 0.01)
@@ -52,6 +52,10 @@ def test_noalloc_field_energy_matches_pic_energy_twice(lib):
         stream.synchronize()
         wf = float(out.item())
         assert abs(wf - wf_ref) <= 1e-12 * abs(wf_ref), (call, wf, wf_ref)
+        # and against a value independent of the library: the definition
+        # W_F = 1/2 dx dy dz sum (E^2 + B^2), summed by numpy on the host
+        wf_np = 0.5 * d[0] * d[1] * d[2] * (float(np.sum(E * E)) + float(np.sum(B * B)))
+        assert abs(wf - wf_np) <= 1e-12 * abs(wf_np), (call, wf, wf_np)
     sim.close()
 
 
