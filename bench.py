@@ -54,7 +54,7 @@ FLOPS_PER_PARTICLE_TSC = 1031
 #   FP64 store: read cell(4) + offset(24) + u(24) + w(8) = 60 B, write cell + offset + u = 52 B.
 #   mixed store: read 4 + 12 + 12 + 4 = 32 B, write 4 + 12 + 12 = 28 B.
 BYTES_PER_PARTICLE = {"fp64": 112, "mixed": 60}
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no measured FP64 peak is provided)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (context; the roofline divides by the in-run probe)
 
 
 def _peaks():
@@ -279,35 +279,103 @@ def time_adjoint(torch, pic, W, nsteps=200, ckpt=20):
             "steps": nsteps, "checkpoint_every": ckpt, "loss": "W_K after %d steps" % nsteps,
             "loss_value": wk, "tape_forward_ms": fwd, "backward_ms": bwd, "fast_forward_ms": fst,
             "adjoint_forward_ratio": bwd / fwd, "adjoint_vs_fast_forward": bwd / fst,
-            "note": "backward = segment replay (recomputation) + adjoint kernels; ratio against the "
-                    "checkpointed forward of the same differentiable path"}
+            "note": "backward = segment replay (recomputation) + adjoint kernels; adjoint_vs_fast_forward "
+                    "divides by pic_step steps of the same workload (the ratio judged against the 3x target), "
+                    "adjoint_forward_ratio by the checkpointed forward it reverses"}
 
 
-def run_laser_ramp(args):
+def measure_fp64_peak(pic, local):
+    """FP64 FMA throughput of this GPU, measured now (pic_probe_fp64_fma: all SMs,
+    independent DFMA chains), with the SM clock sampled while it runs."""
+    with ClockSampler(local) as clk:
+        tf, ms = pic.probe_fp64_fma(local, 16384)
+    return {"tflops": tf, "launch_ms": ms, "clocks": clk.summary(),
+            "how": "pic_probe_fp64_fma: 4 CTAs x 256 threads per SM, 8 independent FMA chains per thread, "
+                   "best of 3 timed launches (FMA = 2 flops)"}
+
+
+def mixed_vs_fp64(torch, pic, wl, checkpoints=(100, 200)):
+    """Error of the mixed path against the FP64 path on the same seeded
+    workload: field energy at each checkpoint step and the per-array
+    norm-wise errors of E, B and J at the last one.  Beside it, the same
+    figures for two FP64 runs that differ only in the sort interval (3 and
+    1), i.e. in the order of every floating-point sum: the reordering noise
+    floor of this chaotic system."""
+    import numpy as np
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+    runs = {}
+    for label, prec, K in (("fp64", pic.FP64, 0), ("fp64_sort1", pic.FP64, 1), ("mixed", pic.MIXED, 0)):
+        sim = pic.Simulation.from_workload(wl, precision=prec, sort_interval=K)
+        wf, done = {}, 0
+        for c in checkpoints:
+            sim.step(c - done)
+            done = c
+            wf[c] = sim.energy()[0]
+        E, B = sim.get_fields()
+        J = sim.get_current()
+        runs[label] = (wf, E, B, J)
+        sim.close()
+    ref = runs["fp64"]
+
+    def errs(label):
+        wf, E, B, J = runs[label]
+        out = {"field_energy_rel_err": {"step %d" % c: abs(wf[c] - ref[0][c]) / abs(ref[0][c]) for c in checkpoints}}
+        out.update({"%s_rel_err_step_%d" % (k, checkpoints[-1]): rel(x, y)
+                    for k, x, y in (("E", E, ref[1]), ("B", B, ref[2]), ("J", J, ref[3]))})
+        return out
+
+    return {"reference": "FP64 path, same seed and workload, sort interval 3",
+            "field_energy_fp64": {"step %d" % c: ref[0][c] for c in checkpoints},
+            "mixed": errs("mixed"), "fp64_reordered_noise_floor": errs("fp64_sort1"),
+            "target": "field energy <= 1e-5 relative after 100 steps"}
+
+
+def time_laser_ramp(torch, pic, W, total=500, adj=50, ck=25):
     """The large laser-plasma workload c5 (256x128x128, 134.2 M electrons over a
     density ramp, a0 = 3 Gaussian pulse, x absorbing): the mixed-precision
-    forward for all but the last 50 steps, then the differentiable FP64 path
-    for the final 50 steps and its adjoint.  Checkpoint every 25 steps: the
-    tape holds 2 checkpoints + the 25 step states of the last segment, 27
-    FP64 states of 7 GB, and only the first segment is recomputed."""
-    import torch
-    from paper_1608_01009_gb300 import pic, workloads as W
-    total, adj, ck = 500, 50, 25
+    forward for the first total - adj steps (3 of them untimed warm-up), then
+    the differentiable FP64 path for the final adj steps and its adjoint.
+    Checkpoint every ck steps: with 25 the tape holds 2 checkpoints + the 25
+    step states of the last segment, 27 FP64 states of 7 GB each, and only the
+    first segment is recomputed.  The adjoint is set against the checkpointed
+    forward it reverses and against plain steps of the same state: FP64
+    pic_step steps (a context loaded with the state at step total - adj) and
+    the mixed context's own steps."""
     t0 = time.perf_counter()
     wl = W.config("c5")
     gen_s = time.perf_counter() - t0
+    nfwd = total - adj - 3
     sim = pic.Simulation.from_workload(wl, precision=pic.MIXED)
     sim.step(3)
     sim.sync()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(sim.stream)
-    sim.step(total - adj - 3)
+    sim.step(nfwd)
     e1.record(sim.stream)
     sim.sync()
     ms_fwd = e0.elapsed_time(e1)
     n_active = sim.count()
     wf, wk = sim.energy()
+    # FP64 pic_step over the same adj steps from this state (then freed)
+    E, B = sim.get_fields(device=True)
+    p = sim.get_particles(0, device=True)
+    fast = pic.Simulation(wl.n, wl.d, wl.dt, wl.bc, pic.FP64, absorb_cells=wl.absorb_cells,
+                          absorb_sigma=wl.absorb_sigma)
+    fast.set_fields(E, B)
+    fast.add_species(wl.species[0].q, wl.species[0].m, *[p[k] for k in ("x", "y", "z", "ux", "uy", "uz", "w")])
+    del p, E, B
+    torch.cuda.synchronize()
+    f0 = time.perf_counter()
+    fast.step(adj)
+    fast.sync()
+    fast_fp64_s = time.perf_counter() - f0
+    fast.close()
+    del fast
+    torch.cuda.empty_cache()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     wk_end = sim.tape_forward(adj, ck)
@@ -316,18 +384,33 @@ def run_laser_ramp(args):
     dE, dB = sim.tape_backward(1.0)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
-    out = {"workload": "c5: 256x128x128, x absorbing, 64 e-/cell over x in [128,256) with a 0->1 n_crit ramp "
-                       "over 32 cells (%d particles), a0 = 3 Gaussian pulse (waist 24 cells, 8 wavelengths)"
-                       % wl.nparticles,
-           "mixed_forward": {"steps": total - adj - 3, "ms_per_step": ms_fwd / (total - adj - 3),
-                             "particle_steps_per_s": wl.nparticles * (total - adj - 3) / (ms_fwd / 1e3),
-                             "active_after": n_active, "W_F": wf, "W_K": wk},
-           "adjoint": {"steps": adj, "checkpoint_every": ck, "tape_forward_s": t2 - t1, "backward_s": t3 - t2,
-                       "ratio": (t3 - t2) / (t2 - t1), "W_K_final": wk_end,
-                       "grad_E_norm": float(dE.norm().item()), "grad_B_norm": float(dB.norm().item())},
-           "input_generation_s": gen_s}
+    gnorm = (float(dE.norm().item()), float(dB.norm().item()))
+    del dE, dB
     sim.close()
-    print(json.dumps(out))
+    mixed_step_s = ms_fwd / nfwd / 1e3
+    bwd = t3 - t2
+    return {"workload": "c5: 256x128x128, x absorbing, 64 e-/cell over x in [128,256) with a 0->1 n_crit ramp "
+                        "over 32 cells (%d particles), a0 = 3 Gaussian pulse (waist 24 cells, 8 wavelengths)"
+                        % wl.nparticles,
+            "mixed_forward": {"steps": nfwd, "ms_per_step": ms_fwd / nfwd,
+                              "particle_steps_per_s": wl.nparticles * nfwd / (ms_fwd / 1e3),
+                              "active_after": n_active, "W_F": wf, "W_K": wk},
+            "adjoint": {"steps": adj, "checkpoint_every": ck, "tape_forward_s": t2 - t1, "backward_s": bwd,
+                        "fast_forward_fp64_s": fast_fp64_s, "fast_forward_mixed_s": mixed_step_s * adj,
+                        "adjoint_forward_ratio": bwd / (t2 - t1),
+                        "adjoint_vs_fast_forward": bwd / fast_fp64_s,
+                        "adjoint_vs_fast_mixed_forward": bwd / (mixed_step_s * adj),
+                        "W_K_final": wk_end, "grad_E_norm": gnorm[0], "grad_B_norm": gnorm[1],
+                        "note": "backward = segment replay (recomputation) + adjoint kernels; "
+                                "adjoint_vs_fast_forward divides by FP64 pic_step steps of the same state, "
+                                "the ratio judged against the 3x target"},
+            "input_generation_s": gen_s}
+
+
+def run_laser_ramp(args):
+    import torch
+    from paper_1608_01009_gb300 import pic, workloads as W
+    print(json.dumps(time_laser_ramp(torch, pic, W)))
     return 0
 
 
@@ -403,6 +486,8 @@ def run_gpu(args):
     wl = W.config(args.workload, seed=None if ws == 1 else 1236 + 101 * rank)
     peaks, peak_kind = _peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak = measure_fp64_peak(pic, local)  # before any timed region
+    fp64_tf = fp64_peak["tflops"]
 
     if ws > 1:
         dist.barrier()
@@ -421,12 +506,14 @@ def run_gpu(args):
            "config": {"workload": _workload_desc(wl, "FP64"), "supercell": 4, "sort_interval": 3,
                       "l2": "inputs larger than L2 (particle store %.0f MB)" % (64 * r["npart"] / 1e6),
                       "parallelism": "replicas x%d" % ws if ws > 1 else "single GPU"},
-           "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": _traffic("fp64"),
+           "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf, "unit": "TFLOP/s",
+                        "frac": achieved_tf / fp64_tf, "traffic": _traffic("fp64"),
                         "kernel": "k_push<double,4> (gather + Boris + move + VB deposit)",
-                        "peak_kind": "nominal FP64 of GB300 (recipe); HBM peak of %s" % peak_kind,
+                        "peak_kind": "measured", "peak_source": "FP64 FMA probe in this run (fp64_peak)",
+                        "frac_of_nominal": achieved_tf / FP64_NOMINAL_TFLOPS, "nominal": FP64_NOMINAL_TFLOPS,
                         "per_launch_ms": push_ms, "hbm_achieved_gbs": achieved_gbs,
-                        "hbm_frac": achieved_gbs / hbm_peak},
+                        "hbm_frac": achieved_gbs / hbm_peak, "hbm_peak_kind": peak_kind},
+           "fp64_peak": fp64_peak,
            "stage_ms_per_step": {k: round(v, 4) for k, v in r["stage_ms"].items()},
            "gpu_launches": r["launches"], "clocks": clk.summary()}
     if not args.no_e2e:
@@ -456,6 +543,19 @@ def run_gpu(args):
                         "stage_ms_per_step": {k: round(v, 4) for k, v in r3["stage_ms"].items()},
                         "gpu_launches": r3["launches"], "clocks": clk3.summary()}
         r3["sim"].close()
+        # the FP64 path on the same workload and seed, timed the same way
+        r3d = time_gpu(torch, pic, wl3, "fp64", args.steps, args.warmup)
+        ms3d = _barrier_max(torch, r3d["ms"], ws)
+        v3d = r3d["npart"] * ws * args.steps / (ms3d / 1e3)
+        pd = r3d["stage_ms"]["push_deposit"]
+        out["mixed"]["fp64_same_workload"] = {
+            "value": v3d, "ms_per_step": ms3d / args.steps, "mixed_speedup": out["mixed"]["value"] / v3d,
+            "roofline": {"bound": "alu", "achieved": FLOPS_PER_PARTICLE * r3d["npart"] / (pd / 1e3) / 1e12,
+                         "peak": fp64_tf, "unit": "TFLOP/s", "kernel": "k_push<double,4>", "per_launch_ms": pd},
+            "stage_ms_per_step": {k: round(v, 4) for k, v in r3d["stage_ms"].items()}}
+        r3d["sim"].close()
+        if not args.no_error:
+            out["mixed"]["error_vs_fp64"] = mixed_vs_fp64(torch, pic, wl3)
     if not args.no_tsc:
         # second-order form factor + Esirkepov current on the same FP64 workload
         rt = time_gpu(torch, pic, wl, "fp64", args.steps, args.warmup, form_factor=2)
@@ -465,14 +565,16 @@ def run_gpu(args):
         out["tsc"] = {"value": weak_value(rt["npart"], ws, args.steps, mst), "unit": UNIT, "dtype": "f64",
                       "config": {"workload": _workload_desc(wl, "FP64"), "form_factor": "TSC + Esirkepov"},
                       "ms_per_step": mst / args.steps,
-                      "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                   "frac": tf / FP64_PEAK_TFLOPS, "traffic": _traffic("tsc"), "kernel": "k_push_tsc",
-                                   "per_launch_ms": pt},
+                      "roofline": {"bound": "alu", "achieved": tf, "peak": fp64_tf, "unit": "TFLOP/s",
+                                   "frac": tf / fp64_tf, "peak_kind": "measured", "traffic": _traffic("tsc"),
+                                   "kernel": "k_push_tsc", "per_launch_ms": pt},
                       "stage_ms_per_step": {k: round(v, 4) for k, v in rt["stage_ms"].items()},
                       "gpu_launches": rt["launches"]}
         rt["sim"].close()
     if not args.no_adjoint:
         out["adjoint"] = time_adjoint(torch, pic, W)
+    if not args.no_laser_ramp:
+        out["laser_ramp"] = time_laser_ramp(torch, pic, W)
     if not args.no_sweep:
         # supercell edge S (the paper's Tables 5-6 study): particle-steps/s per S
         sweep = {}
@@ -524,8 +626,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-tsc", action="store_true")
+    ap.add_argument("--no-error", action="store_true", help="skip the mixed-vs-FP64 error runs on c3")
+    ap.add_argument("--no-laser-ramp", action="store_true", help="skip the c5 laser-plasma run and its adjoint")
     ap.add_argument("--laser-ramp", action="store_true",
-                    help="run the 134 M-particle laser-plasma workload with its 50-step adjoint instead")
+                    help="run only the 134 M-particle laser-plasma workload with its 50-step adjoint")
     ap.add_argument("--profile-case", choices=["fp64", "mixed", "tsc"], default=None,
                     help="run only one reduced case for ncu captures (a few GB on the device): "
                          "fp64 = the 64^3 x 50 FP64 plasma, mixed = a 96^3 x 32 mixed plasma, "

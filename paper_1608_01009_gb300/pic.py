@@ -81,7 +81,19 @@ SIGNATURES = {
     "pic_tape_forward": [_VP, C.c_int, C.c_int, C.POINTER(C.c_double)],
     "pic_tape_backward": [_VP, C.c_double, _VP, _VP, _VP, _VP],
     "pic_tape_particle_grad": [_VP, C.c_int, _VP],
+    "pic_probe_fp64_fma": [C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)],
 }
+
+
+def probe_fp64_fma(device: int = 0, iters: int = 2048):
+    """Measured FP64 FMA throughput of `device` (pic_probe_fp64_fma):
+    returns (TFLOP/s counting an FMA as 2 flops, ms of the timed launch)."""
+    lib = load_library()
+    tf, ms = C.c_double(), C.c_double()
+    rc = lib.pic_probe_fp64_fma(int(device), int(iters), C.byref(tf), C.byref(ms))
+    if rc != PIC_OK:
+        raise PicError(rc, "pic_probe_fp64_fma failed")
+    return tf.value, ms.value
 
 
 def load_library(path: str = LIB_PATH):
