@@ -46,13 +46,39 @@ __device__ __forceinline__ double stag(int comp, int axis, bool magnetic) {
     return magnetic ? (comp == axis ? 0.0 : 0.5) : (comp == axis ? 0.5 : 0.0);
 }
 
-// Lattice base and fractions of component c (0..5: Ex..Ez, Bx..Bz) at xi.
-__device__ __forceinline__ void lattice(int c, const double xi[3], int base[3], double f[3]) {
+// Cell of xi along each axis and the two lattices a component can sit on:
+// the node lattice (base = cell, fraction = offset a in [0,1)) and the
+// half-shifted one (xi - 1/2: base cell - 1 and a + 1/2 when a < 1/2, else
+// cell and a - 1/2).  One floor and one conversion per axis serve all six
+// components, whose lattices are these per axis (the floor and the FP64 ->
+// int conversion run on the FP64 pipe, which bounds the differentiable path).
+struct Lat {
+    int c0[3], c1[3];      // base on the node / half-shifted lattice
+    double f0[3], f1[3];   // fractions
+};
+
+__device__ __forceinline__ Lat lattices(const double xi[3]) {
+    Lat L;
     for (int a = 0; a < 3; ++a) {
-        const double s = xi[a] - stag(c % 3, a, c >= 3);
-        const double fl = floor(s);
-        base[a] = (int)fl;
-        f[a] = s - fl;
+        const double fl = floor(xi[a]);
+        const int ci = (int)fl;
+        const double o = xi[a] - fl;
+        const bool lo = __double2hiint(o) < 0x3FE00000;  // o < 1/2 (o >= 0: bit patterns order like integers)
+        L.c0[a] = ci;
+        L.f0[a] = o;
+        L.c1[a] = lo ? ci - 1 : ci;
+        L.f1[a] = o + (lo ? 0.5 : -0.5);
+    }
+    return L;
+}
+
+// Lattice base and fractions of component c (0..5: Ex..Ez, Bx..Bz).
+__device__ __forceinline__ void lattice(int c, const Lat& L, int base[3], double f[3]) {
+    for (int a = 0; a < 3; ++a) {
+        // E_c is half-shifted along axis c, B_c along the two other axes
+        const bool half = c < 3 ? c == a : c - 3 != a;
+        base[a] = half ? L.c1[a] : L.c0[a];
+        f[a] = half ? L.f1[a] : L.f0[a];
     }
 }
 
@@ -96,8 +122,8 @@ __device__ void boris_adjoint(const double u[3], const double E[3], const double
                               double lu[3], double lE[3], double lB[3]) {
     double um[3], t[3], s[3], up[3];
     for (int a = 0; a < 3; ++a) um[a] = fma(h, E[a], u[a]);
-    const double gm = sqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], 1.0))));
-    const double gg = h / gm;
+    const double rgm = rsqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], 1.0))));  // 1 / gamma^-
+    const double gg = h * rgm;
     for (int a = 0; a < 3; ++a) t[a] = gg * B[a];
     const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
     const double k = 2.0 / (1.0 + t2);
@@ -124,8 +150,9 @@ __device__ void boris_adjoint(const double u[3], const double E[3], const double
     // t = g B, g = h / gm, gm = sqrt(1 + um.um)
     const double lg = lt[0] * B[0] + lt[1] * B[1] + lt[2] * B[2];
     for (int a = 0; a < 3; ++a) lB[a] += gg * lt[a];
-    const double lgm = -lg * gg / gm;
-    for (int a = 0; a < 3; ++a) lum[a] += lgm * um[a] / gm;
+    // d gamma^- / d um = um / gamma^-, d g / d gamma^- = -g / gamma^-
+    const double lgm = -lg * gg * rgm;
+    for (int a = 0; a < 3; ++a) lum[a] += (lgm * rgm) * um[a];
     // um = u + h E
     for (int a = 0; a < 3; ++a) {
         lu[a] = lum[a];
@@ -299,11 +326,12 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, S
     const GridDev& g = sp.g;
     double xi[3] = {T.xi[0][p], T.xi[1][p], T.xi[2][p]};
     double u[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
+    const Lat lat = lattices(xi);
     double F[6];
     for (int c = 0; c < 6; ++c) {
         int base[3];
         double f[3], v[8];
-        lattice(c, xi, base, f);
+        lattice(c, lat, base, f);
         corners(EB, g, c, base, v);
         F[c] = tri_val(v, f);
     }
@@ -313,9 +341,8 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, S
     int cell0[3];
     for (int c = 0; c < 3; ++c) {
         d[c] = u[c] * (gi * sp.dtd[c]);
-        const double fl = floor(xi[c]);
-        cell0[c] = (int)fl;
-        a[c] = xi[c] - fl;
+        cell0[c] = lat.c0[c];
+        a[c] = lat.f0[c];
     }
     const double w = T.w[p];
     if (w != 0.0 && sp.cq[0] != 0.0) {
@@ -365,11 +392,12 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     const double u0[3] = {T.u[0][p], T.u[1][p], T.u[2][p]};
     // recompute the forward gather, with the position derivatives of each
     // interpolant from the same lerp tree: v = lerp_z(lerp_y(lerp_x(corners)))
+    const Lat lat = lattices(xi);
     double F[6], dF[6][3], fr[6][3];
     int bs[6][3];
     for (int c = 0; c < 6; ++c) {
         double v[8];
-        lattice(c, xi, bs[c], fr[c]);
+        lattice(c, lat, bs[c], fr[c]);
         corners(EB, g, c, bs[c], v);
         const double* f = fr[c];
         const double a0 = v[1] - v[0], a1 = v[3] - v[2], a2 = v[5] - v[4], a3 = v[7] - v[6];
@@ -391,9 +419,8 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     int cell0[3];
     for (int c = 0; c < 3; ++c) {
         d[c] = u1[c] * (gi * sp.dtd[c]);
-        const double fl = floor(xi[c]);
-        cell0[c] = (int)fl;
-        a[c] = xi[c] - fl;
+        cell0[c] = lat.c0[c];
+        a[c] = lat.f0[c];
     }
     // cotangents of the outputs
     double lx1[3] = {L.xi[0][p], L.xi[1][p], L.xi[2][p]};

@@ -378,6 +378,9 @@ int push_species_tsc(pic_ctx* c, Species& s) {
 
 template <class R>
 int alloc_store(pic_ctx* c, Species& s, Store<R>& st, long long cap) {
+    // the FP32 particle kernel reads and writes four particles at a time with
+    // 16-byte accesses: every array holds a whole number of such groups
+    cap = (cap + 3) & ~3LL;
     for (int b = 0; b < 2; ++b) {
         PStore<R>& p = st.buf[b];
         int r = dalloc(c, s.allocs, &p.cell, cap);
@@ -1073,7 +1076,7 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
         return bail(r);
     if (bps < 1) bps = 1;
     c->push_grid = c->nsm * bps;
-    if (!c->mixed && (r = alloc_xqueue<double>(c))) return bail(r);  // the FP32 kernel splits in the warp
+    if ((r = c->mixed ? alloc_xqueue<float>(c) : alloc_xqueue<double>(c))) return bail(r);
     *out = c;
     return PIC_OK;
 }

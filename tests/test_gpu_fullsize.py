@@ -9,6 +9,8 @@ state (fields grown by the plasma or the pulse inside the plasma, particles
 drifted and re-sorted) is checked through:
 * sampled particles, pushed one by one by the oracle from the same state
   (gather, Boris, move) -- positions and momenta element by element;
+* the whole current J^{n+1/2}, element by element, against the oracle's
+  deposit of every particle from the same state (pushed in chunks; c2 and c3);
 * the discrete charge continuity (rho^{n+1} - rho^n)/dt + div J = 0 of the
   GPU's current against the CIC (or TSC) rho of all GPU particles (a property that holds
   at any size);
@@ -41,7 +43,8 @@ def _sampled(p, ids):
     return [p[k][where[ids]] for k in KEYS]
 
 
-def _full_size_check(name, precision, warm, nsample, tol_x, tol_u, tol_fields, tol_cont, form_factor=1):
+def _full_size_check(name, precision, warm, nsample, tol_x, tol_u, tol_fields, tol_cont, form_factor=1,
+                     tol_J=None):
     wl = W.config(name)
     sim = P.Simulation.from_workload(wl, precision=precision, supercell=4, form_factor=form_factor)
     n, q, m = wl.nparticles, wl.species[0].q, wl.species[0].m
@@ -65,6 +68,15 @@ def _full_size_check(name, precision, warm, nsample, tol_x, tol_u, tol_fields, t
     assert p["x"].shape[0] == n
     s0 = _sampled(p, ids)
     r0 = rho(p)
+    Jo = None
+    if tol_J is not None:
+        # the oracle's current of every particle from this state (gather, push, move,
+        # deposit), summed over chunks into one grid
+        ora = O.Oracle(*grid, E0, B0, **kw)
+        for a in range(0, p["x"].shape[0], CHUNK):
+            ora.push_deposit(O.OracleSpecies(q, m, *[p[k][a:a + CHUNK] for k in KEYS]))
+        Jo = ora.J
+        del ora
     del p
     sim.step(1)
     sim.sync()
@@ -87,6 +99,11 @@ def _full_size_check(name, precision, warm, nsample, tol_x, tol_u, tol_fields, t
         e = PT.rel_err(s1[3 + a], osp.arr[3 + a])
         assert e <= tol_u, (k, e)
 
+    # the whole current, element by element (norm-wise per component array)
+    if Jo is not None:
+        e = PT.rel_err(J, Jo)
+        assert e <= tol_J, ("J", e)
+
     # charge continuity of the GPU current over every particle
     divJ = O.Oracle(*grid, **kw).div(J)
     assert np.max(np.abs(divJ)) > 0
@@ -105,7 +122,7 @@ def _full_size_check(name, precision, warm, nsample, tol_x, tol_u, tol_fields, t
 
 def test_c2_full_size_fp64():
     _full_size_check("c2", P.FP64, warm=7, nsample=200_000, tol_x=1e-12, tol_u=1e-12, tol_fields=1e-12,
-                     tol_cont=1e-11)
+                     tol_cont=1e-11, tol_J=1e-12)
 
 
 def test_c2_full_size_tsc():
@@ -117,8 +134,9 @@ def test_c2_full_size_tsc():
 def test_c3_full_size_mixed():
     # FP32 state: positions/momenta at FP32 rounding against the FP64 oracle step
     # from the same (FP32-rounded) state; continuity and Yee are exact in FP64
+    # J: FP32 gather, push and current sums against the FP64 oracle from the same state
     _full_size_check("c3", P.MIXED, warm=4, nsample=200_000, tol_x=1e-6, tol_u=1e-6, tol_fields=1e-12,
-                     tol_cont=1e-5)
+                     tol_cont=1e-5, tol_J=1e-5)
 
 
 def test_c5_full_size_mixed_laser_ramp():
