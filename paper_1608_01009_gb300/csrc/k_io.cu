@@ -162,6 +162,25 @@ __global__ void k_energy_finalize(const double* __restrict__ wf_part, int nwf, c
     }
 }
 
+// Largest |w| of an FP32 store (non-negative floats order like their bit
+// patterns, so an unsigned atomicMax on the bits is a float max).
+__global__ void __launch_bounds__(IO_NT) k_wmax(const float* __restrict__ w, const long long* __restrict__ n_cur,
+                                               float* __restrict__ wmax) {
+    const long long N = *n_cur;
+    unsigned m = 0;
+    for (long long p = (long long)blockIdx.x * IO_NT + threadIdx.x; p < N; p += (long long)gridDim.x * IO_NT)
+        m = max(m, __float_as_uint(fabsf(w[p])));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned*>(wmax), m);
+}
+
+cudaError_t wmax_launch(cudaStream_t st, int nsm, const float* w, const long long* n, float* wmax) {
+    cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    k_wmax<<<nsm * 4, IO_NT, 0, st>>>(w, n, wmax);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t load_launch(cudaStream_t st, long long n, const double* const* src7, const PStore<R>& dst,
                         const GridDev& g) {

@@ -75,6 +75,7 @@ struct Species {
     Chunk* d_chunks = nullptr;
     int* d_nchunks = nullptr;
     double* d_ek = nullptr;        // kinetic-energy partials of the last push (push_grid entries)
+    float* d_wmax = nullptr;       // mixed: largest |w| of the store (scale of the fixed-point current)
     double* d_stage = nullptr;     // 7 x cap FP64 staging area for host uploads (allocated on first use)
     // asynchronous upload (pic_upload_particles): 7 x up_cap FP64 arrays filled on
     // the copy stream; up_n >= 0 while an upload waits to be consumed.  Not part
@@ -258,9 +259,14 @@ int encode_tmap(pic_ctx* c, CUtensorMap* map, void* base, bool fp32) {
 template <class R>
 int push_dispatch_setup(pic_ctx* c, int S, int* bps) {
     cudaError_t e = cudaErrorInvalidValue;
-    if (S == 2) e = push_setup<double, 2>(bps);
-    if (S == 4) e = push_setup<R, 4>(bps);
-    if (S == 8) e = push_setup<R, 8>(bps);
+    if constexpr (sizeof(R) == 4) {
+        if (S == 4) e = push32_setup<4>(bps);
+        if (S == 8) e = push32_setup<8>(bps);
+    } else {
+        if (S == 2) e = push_setup<double, 2>(bps);
+        if (S == 4) e = push_setup<double, 4>(bps);
+        if (S == 8) e = push_setup<double, 8>(bps);
+    }
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push kernel setup: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
@@ -274,6 +280,7 @@ PushParams make_params(const pic_ctx* c, const Species& s) {
         pp.cq[a] = s.q / (c->g.dt * c->g.d[(a + 1) % 3] * c->g.d[(a + 2) % 3]);
     }
     pp.mass = s.m;
+    pp.wmax = s.d_wmax;
     pp.qdt2m_f = (float)pp.qdt2m;
     for (int a = 0; a < 3; ++a) {
         pp.dtd_f[a] = (float)pp.dtd[a];
@@ -356,11 +363,18 @@ int push_species(pic_ctx* c, Species& s) {
         if (S == 2)
             e = push_launch<double, 2>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
                                        c->d_err);
+        if (S == 4)
+            e = push_launch<double, 4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
+                                       c->d_err);
+        if (S == 8)
+            e = push_launch<double, 8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
+                                       c->d_err);
+    } else {
+        if (S == 4)
+            e = push32_launch<4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+        if (S == 8)
+            e = push32_launch<8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
     }
-    if (S == 4)
-        e = push_launch<R, 4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
-    if (S == 8)
-        e = push_launch<R, 8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push launch: %s", cudaGetErrorString(e));
     c->launches += 1;
     return PIC_OK;
@@ -406,6 +420,7 @@ void free_species(Species& s) {
     s.d_chunks = nullptr;
     s.d_nchunks = nullptr;
     s.d_stage = nullptr;
+    s.d_wmax = nullptr;
 }
 
 // Device address of a page-locked host array (cudaHostAlloc / cudaHostRegister,
@@ -429,11 +444,22 @@ int alloc_species(pic_ctx* c, Species& s, long long n) {
     if (!r) r = dalloc(c, s.allocs, &s.d_bin_start, (size_t)c->g.nbins + 1);
     if (!r) r = dalloc(c, s.allocs, &s.d_chunks, (size_t)(c->g.nbins + cap / CHUNK + 1));
     if (!r) r = dalloc(c, s.allocs, &s.d_nchunks, 1);
+    if (!r) r = dalloc(c, s.allocs, &s.d_wmax, 1);
     if (!r) r = c->mixed ? alloc_store(c, s, s.s32, cap) : alloc_store(c, s, s.s64, cap);
     if (r) return r;
+    CUDA_TRY(c, cudaMemsetAsync(s.d_wmax, 0, sizeof(float), c->st));
     CUDA_TRY(c, cudaMemsetAsync(s.d_nchunks, 0, sizeof(int), c->st));
     // an immobile species is never sorted: its (empty) bins stay at 0
     CUDA_TRY(c, cudaMemsetAsync(s.d_bin_start, 0, ((size_t)c->g.nbins + 1) * sizeof(int), c->st));
+    return PIC_OK;
+}
+
+// Largest |w| of a mixed-precision store (the fixed-point current's scale).
+int refresh_wmax(pic_ctx* c, Species& s) {
+    if (!c->mixed || !s.d_wmax) return PIC_OK;
+    cudaError_t e = wmax_launch(c->st, c->nsm, s.s32.a().w, s.d_n, s.d_wmax);
+    c->launches += 1;
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "wmax: %s", cudaGetErrorString(e));
     return PIC_OK;
 }
 
@@ -472,6 +498,7 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
     // bin the new particles; the other species are re-sorted too, so that every
     // species starts the next sort interval together
     r = sort_all(c);
+    if (!r) r = refresh_wmax(c, s);
     c->energy_fresh = false;
     return r;
 }
@@ -1516,6 +1543,7 @@ int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
                                         c->st));
         }
         CUDA_TRY(c, cudaMemcpyAsync(s.d_nchunks, &sh.nchunks, sizeof(int), cudaMemcpyHostToDevice, c->st));
+        if ((r = refresh_wmax(c, s))) return r;
         // the host values above are locals: finish the copies before they go out of scope
         CUDA_TRY(c, cudaStreamSynchronize(c->st));
     }

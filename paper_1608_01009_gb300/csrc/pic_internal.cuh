@@ -72,6 +72,9 @@ struct PushParams {
     // FP32 copies for the mixed kernel (a double -> float conversion runs on
     // the FP64 pipe, so none is left inside the particle loop)
     float qdt2m_f, dtd_f[3], cq_f[3];
+    // mixed kernel: the species' largest |w| (device, written by the load), which
+    // fixes the scale of the fixed-point current tile
+    const float* wmax;
 };
 
 // Per-CTA queue of the moves that leave their start cell (structure of arrays,
@@ -219,11 +222,21 @@ __device__ double block_sum(double v, double* scratch) {
 }
 
 // ------------------------------------------------------------------ launchers (host)
+cudaError_t wmax_launch(cudaStream_t st, int nsm, const float* w, const long long* n, float* wmax);
+
+// FP64 particle kernel (k_push.cu, R = double, S = 2, 4, 8)
 template <class R, int S>
 cudaError_t push_setup(int* blocks_per_sm);
 template <class R, int S>
 cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
                         const XQueue<R>& xq, const Chunk* chunks, const int* nchunks, double* J, double* ek_part,
                         int* err);
+// mixed-precision particle kernel (k_push32.cu, S = 4, 8)
+template <int S>
+cudaError_t push32_setup(int* blocks_per_sm);
+template <int S>
+cudaError_t push32_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp,
+                          const PStore<float>& ps, const XQueue<float>& xq, const Chunk* chunks, const int* nchunks,
+                          double* J, double* ek_part, int* err);
 
 }  // namespace picgb
