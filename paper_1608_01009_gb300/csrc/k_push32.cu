@@ -27,9 +27,17 @@ namespace picgb {
 //   * moves that leave their start cell are queued per CTA (global memory,
 //     one slot per particle of the chunk) and split into Villasenor-Buneman
 //     pieces by all threads after the chunk.
-// Measured on the 128^3 x 32 workload: 3.62 ms per launch with one particle
-// per lane and a warp scan, 3.38 ms with two per thread, 2.82 ms with the
-// fixed-point tile (4 particles per thread: 2.92 ms, fewer resident warps).
+//   * 32-bit integer atomics to one address still serialise (about one cycle
+//     per lane), so each thread sums two consecutive groups (4 particles)
+//     before it adds: a cell's run covers half as many lanes and each lane
+//     adds half as often.
+// Measured on the 128^3 x 32 workload (67.1 M particles): 3.62 ms per launch
+// with one particle per lane and a warp scan, 3.38 ms with two per thread,
+// 2.82 ms with the fixed-point tile, 2.38 ms with two groups per thread
+// between adds (one group: 2.78, four: 2.70, eight: 3.15 ms; 4 CTAs per SM at
+// 64 registers: 3.10 ms; the lanes of a cell summed by the hardware integer
+// reduction before one lane adds: 3.97 ms).  On the 134 M-particle laser
+// ramp (64 per cell) after 450 steps: 7.16 ms with one group, 4.58 ms with two.
 // A chunk may start at any particle: the groups overlapping its ends mask the
 // particles outside it and store element by element.
 #ifndef PICGB_PUSHG_MINB
@@ -37,6 +45,12 @@ namespace picgb {
 #endif
 #ifndef PICGB_PG
 #define PICGB_PG 2
+#endif
+#ifndef PICGB_GM
+#define PICGB_GM 2  // consecutive groups per thread between flushes of its register sums
+#endif
+#ifndef PICGB_FLUSH_REDUX
+#define PICGB_FLUSH_REDUX 0  // 1: lanes of one cell summed by the warp's integer reduction before one lane's atomics
 #endif
 constexpr int PG = PICGB_PG;  // particles per thread: 2 (8-byte accesses) or 4 (16-byte accesses)
 template <int G>
@@ -101,16 +115,33 @@ __device__ __forceinline__ void fx_split(float v, float s, int& hi, int& lo) {
     lo = __float_as_int(fmaf(r, (float)(1 << FX_LO_BITS), FX_MAGIC)) - __float_as_int(FX_MAGIC);
 }
 
+// The same split for a pair of values with packed two-wide FP32 instructions.
+__device__ __forceinline__ void fx_split2(float v0, float v1, float s, int (&hi)[2], int (&lo)[2]) {
+    const float2 M = make_float2(FX_MAGIC, FX_MAGIC);
+    const float2 x = __fmul2_rn(make_float2(v0, v1), make_float2(s, s));
+    const float2 t = __fadd2_rn(x, M);
+    const float2 d = __fadd2_rn(t, make_float2(-FX_MAGIC, -FX_MAGIC));  // round(x), exact
+    const float2 r = __fadd2_rn(x, make_float2(-d.x, -d.y));
+    const float2 t2 = __ffma2_rn(r, make_float2((float)(1 << FX_LO_BITS), (float)(1 << FX_LO_BITS)), M);
+    const int m = __float_as_int(FX_MAGIC);
+    hi[0] = __float_as_int(t.x) - m;
+    hi[1] = __float_as_int(t.y) - m;
+    lo[0] = __float_as_int(t2.x) - m;
+    lo[1] = __float_as_int(t2.y) - m;
+}
+
 template <int TJ>
 __device__ __forceinline__ void add12i(int* Ji, int key, const float (&a)[12], float s) {
     constexpr int LO = 3 * TJ * TJ * TJ;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        int hi, lo;
-        fx_split(a[i], s, hi, lo);
-        const int o = key + edge_offset<TJ>(i);
-        atomicAdd(Ji + o, hi);
-        atomicAdd(Ji + LO + o, lo);
+    for (int i = 0; i < 12; i += 2) {
+        int hi[2], lo[2];
+        fx_split2(a[i], a[i + 1], s, hi, lo);
+        const int o0 = key + edge_offset<TJ>(i), o1 = key + edge_offset<TJ>(i + 1);
+        atomicAdd(Ji + o0, hi[0]);
+        atomicAdd(Ji + o1, hi[1]);
+        atomicAdd(Ji + LO + o0, lo[0]);
+        atomicAdd(Ji + LO + o1, lo[1]);
     }
 }
 
@@ -219,8 +250,14 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         const int start = ch.start, end = ch.start + ch.count;
         const int ga = start / PG, gb = (end + PG - 1) / PG;
         float ek_chunk = 0.0f;
-        for (int gw = ga + warp * 32; gw < gb; gw += NT) {
-            const int gq = gw + lane, p0 = gq * PG;
+        for (int gw = ga + warp * 32 * PICGB_GM; gw < gb; gw += NT * PICGB_GM) {
+          float acc[12];
+#pragma unroll
+          for (int i = 0; i < 12; ++i) acc[i] = 0.0f;
+          int kacc = -1;
+#pragma unroll 1
+          for (int gm = 0; gm < PICGB_GM; ++gm) {
+            const int gq = gw + lane * PICGB_GM + gm, p0 = gq * PG;
             const bool gv = gq < gb;
             VecI c4;
 #pragma unroll
@@ -308,10 +345,6 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
             // Phase B: move, Villasenor-Buneman deposit (a move inside its start
             // cell joins the thread's running sum; a move that leaves it is
             // queued), new cell and offset, kinetic energy
-            float acc[12];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) acc[i] = 0.0f;
-            int kacc = -1;
 #pragma unroll
             for (int j = 0; j < PG; ++j) {
                 const int ki = kinfo[j];
@@ -393,7 +426,6 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                 }
             }
             if (bad) atomicOr(err, ERRBIT_DRIFT);
-            if (kacc >= 0) add12i<TJ>(Ji, kacc, acc, fxs);
             if (gv) {
                 if (p0 >= start && p0 + PG <= end) {
                     *reinterpret_cast<VecI*>(ps.cell + p0) = c4;
@@ -419,6 +451,36 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                     }
                 }
             }
+        }  // groups of this thread
+#if PICGB_FLUSH_REDUX
+          {
+            // the lanes holding one cell (consecutive in the warp) summed by the
+            // hardware integer reduction; the lowest of them adds the totals
+            const unsigned peers = __match_any_sync(FULL, kacc);
+            int hi[12], lo[12];
+#pragma unroll
+            for (int i = 0; i < 12; i += 2) {
+                int h2[2], l2[2];
+                fx_split2(acc[i], acc[i + 1], fxs, h2, l2);
+                hi[i] = h2[0], hi[i + 1] = h2[1], lo[i] = l2[0], lo[i + 1] = l2[1];
+            }
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                hi[i] = __reduce_add_sync(peers, hi[i]);
+                lo[i] = __reduce_add_sync(peers, lo[i]);
+            }
+            if (kacc >= 0 && lane == __ffs(peers) - 1) {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    const int o = kacc + edge_offset<TJ>(i);
+                    atomicAdd(Ji + o, hi[i]);
+                    atomicAdd(Ji + 3 * TJ3 + o, lo[i]);
+                }
+            }
+          }
+#else
+          if (kacc >= 0) add12i<TJ>(Ji, kacc, acc, fxs);
+#endif
         }
         ek += (double)ek_chunk;
         __syncthreads();
