@@ -49,9 +49,6 @@ namespace picgb {
 #ifndef PICGB_GM
 #define PICGB_GM 2  // consecutive groups per thread between flushes of its register sums
 #endif
-#ifndef PICGB_FLUSH_REDUX
-#define PICGB_FLUSH_REDUX 0  // 1: lanes of one cell summed by the warp's integer reduction before one lane's atomics
-#endif
 constexpr int PG = PICGB_PG;  // particles per thread: 2 (8-byte accesses) or 4 (16-byte accesses)
 template <int G>
 struct GVec;
@@ -452,35 +449,8 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                 }
             }
         }  // groups of this thread
-#if PICGB_FLUSH_REDUX
-          {
-            // the lanes holding one cell (consecutive in the warp) summed by the
-            // hardware integer reduction; the lowest of them adds the totals
-            const unsigned peers = __match_any_sync(FULL, kacc);
-            int hi[12], lo[12];
-#pragma unroll
-            for (int i = 0; i < 12; i += 2) {
-                int h2[2], l2[2];
-                fx_split2(acc[i], acc[i + 1], fxs, h2, l2);
-                hi[i] = h2[0], hi[i + 1] = h2[1], lo[i] = l2[0], lo[i + 1] = l2[1];
-            }
-#pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                hi[i] = __reduce_add_sync(peers, hi[i]);
-                lo[i] = __reduce_add_sync(peers, lo[i]);
-            }
-            if (kacc >= 0 && lane == __ffs(peers) - 1) {
-#pragma unroll
-                for (int i = 0; i < 12; ++i) {
-                    const int o = kacc + edge_offset<TJ>(i);
-                    atomicAdd(Ji + o, hi[i]);
-                    atomicAdd(Ji + 3 * TJ3 + o, lo[i]);
-                }
-            }
-          }
-#else
           if (kacc >= 0) add12i<TJ>(Ji, kacc, acc, fxs);
-#endif
+
         }
         ek += (double)ek_chunk;
         __syncthreads();
