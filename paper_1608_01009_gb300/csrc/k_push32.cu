@@ -38,6 +38,9 @@ namespace picgb {
 // 64 registers: 3.10 ms; the lanes of a cell summed by the hardware integer
 // reduction before one lane adds: 3.97 ms).  On the 134 M-particle laser
 // ramp (64 per cell) after 450 steps: 7.16 ms with one group, 4.58 ms with two.
+//   * lanes add to two copies of the tile (lane parity), which halves the lanes
+//     of one cell that meet at one address: 2.36 -> 2.27 ms (four copies: 2.46
+//     ms, the copies' zeroing and merge outweigh it); laser ramp 4.55 -> 4.04 ms.
 // A chunk may start at any particle: the groups overlapping its ends mask the
 // particles outside it and store element by element.
 #ifndef PICGB_PUSHG_MINB
@@ -199,7 +202,11 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
     const float h = pp.qdt2m_f;
     const float dtdx = pp.dtd_f[0], dtdy = CU ? dtdx : pp.dtd_f[1], dtdz = CU ? dtdx : pp.dtd_f[2];
     const float cqx = pp.cq_f[0], cqy = CU ? cqx : pp.cq_f[1], cqz = CU ? cqx : pp.cq_f[2];
-    int* Ji = reinterpret_cast<int*>(Jt);
+    // this lane's copy of the fixed-point tile: lanes next to each other (often of
+    // one cell) add to different copies, so fewer of them hit one address
+    constexpr int NCP = Tile<float, S>::FX_COPIES;
+    int* const Jall = reinterpret_cast<int*>(Jt);
+    int* const Ji = Jall + (lane % NCP) * 6 * TJ3;
     // scale of the fixed-point tile: the largest value a move can deposit is below
     // max|cq| w_max max(dt/d) (1 + max(dt/d)^2 / 12) < 1.25 max|cq| w_max max(dt/d)
     float fxs = 1.0f;
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
             tma_load_4d(F, &tmEB, c0x, c0y, c0z, 0, &bar);
         }
         if (!kCoef)
-            for (int i = threadIdx.x; i < 6 * TJ3; i += NT) Ji[i] = 0;
+            for (int i = threadIdx.x; i < NCP * 6 * TJ3; i += NT) Jall[i] = 0;
         const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT, WAIT_LIMIT_NS);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         if (kCoef) {
             build_coef<float, T, NT>(F, X);
             __syncthreads();
-            for (int i = threadIdx.x; i < 6 * TJ3; i += NT) Ji[i] = 0;  // the tile over the raw tile
+            for (int i = threadIdx.x; i < NCP * 6 * TJ3; i += NT) Jall[i] = 0;  // the tile over the raw tile
             __syncthreads();
         }
         const int start = ch.start, end = ch.start + ch.count;
@@ -466,7 +473,12 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         if (threadIdx.x == 0) s_qn = 0;
         // merge: J tile cell t is domain cell c0 - 1 + t, padded index c0 + 1 + t
         for (int i = threadIdx.x; i < 3 * TJ3; i += NT) {
-            const int hi = Ji[i], lo = Ji[3 * TJ3 + i];
+            int hi = 0, lo = 0;
+#pragma unroll
+            for (int cpy = 0; cpy < NCP; ++cpy) {
+                hi += Jall[cpy * 6 * TJ3 + i];
+                lo += Jall[cpy * 6 * TJ3 + 3 * TJ3 + i];
+            }
             if ((hi | lo) != 0) {
                 const int comp = i / TJ3, r = i - comp * TJ3;
                 const int tz = r / (TJ * TJ), ty = (r / TJ) % TJ, tx = r % TJ;

@@ -20,6 +20,9 @@ __device__ __forceinline__ R lerp(R a, R b, R t) {
 #ifndef PICGB_MOMENTS
 #define PICGB_MOMENTS 1
 #endif
+#ifndef PICGB_FX_COPIES
+#define PICGB_FX_COPIES 2
+#endif
 template <class R, int S>
 struct Tile {
     static constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
@@ -28,9 +31,13 @@ struct Tile {
     // FP64 with a coefficient tile accumulates the deposit's 12 moments per
     // cell (see value_offset) instead of the 3 edge components
     static constexpr bool kMoments = PICGB_MOMENTS && sizeof(R) == 8 && kCoef;
-    // accumulation tile (elements): FP64 12 moments per cell; FP32 the 3 edge
-    // components per cell as two 32-bit fixed-point parts
-    static constexpr int ACC = kMoments ? 12 * TJ3 : (sizeof(R) == 4 ? 6 * TJ3 : 3 * TJ3);
+    // accumulation tile (elements): FP64 12 moments per cell, or the 3 edge
+    // components per cell without a coefficient tile;
+    // FP32: FX_COPIES copies of the 3 edge components per cell as two 32-bit
+    // fixed-point parts (lanes spread over the copies; one copy without a
+    // coefficient tile, whose raw tile is kept)
+    static constexpr int FX_COPIES = sizeof(R) == 4 && kCoef ? PICGB_FX_COPIES : 1;
+    static constexpr int ACC = kMoments ? 12 * TJ3 : (sizeof(R) == 4 ? FX_COPIES * 6 * TJ3 : 3 * TJ3);
     static constexpr int RAW = 6 * T3 > ACC ? 6 * T3 : ACC;           // raw tile region, re-used for it
 };
 
