@@ -95,64 +95,63 @@ __device__ __forceinline__ void corners(const double* EB, const GridDev& g, int 
     for (int q = 0; q < 8; ++q) v[q] = F[pidx(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1), base[2] + (q >> 2))];
 }
 
-__device__ __forceinline__ void boris(double u[3], const double E[3], const double B[3], double h) {
-    double um[3], t[3], s[3], up[3];
-    for (int a = 0; a < 3; ++a) um[a] = fma(h, E[a], u[a]);
-    const double hg = h * rsqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], 1.0))));
-    for (int a = 0; a < 3; ++a) t[a] = hg * B[a];
-    const double k = 2.0 / (1.0 + fma(t[0], t[0], fma(t[1], t[1], t[2] * t[2])));
-    for (int a = 0; a < 3; ++a) s[a] = k * t[a];
-    up[0] = fma(um[1], t[2], fma(-um[2], t[1], um[0]));
-    up[1] = fma(um[2], t[0], fma(-um[0], t[2], um[1]));
-    up[2] = fma(um[0], t[1], fma(-um[1], t[0], um[2]));
-    u[0] = fma(h, E[0], fma(up[1], s[2], fma(-up[2], s[1], um[0])));
-    u[1] = fma(h, E[1], fma(up[2], s[0], fma(-up[0], s[2], um[1])));
-    u[2] = fma(h, E[2], fma(up[0], s[1], fma(-up[1], s[0], um[2])));
-}
-
 __device__ __forceinline__ void cross(const double a[3], const double b[3], double c[3]) {
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Reverse mode of the Boris step: given lun (cotangent of the new u), returns
-// lu (old u) and adds the cotangents of the particle fields into lE, lB.
-__device__ void boris_adjoint(const double u[3], const double E[3], const double B[3], double h, const double lun[3],
-                              double lu[3], double lE[3], double lB[3]) {
-    double um[3], t[3], s[3], up[3];
-    for (int a = 0; a < 3; ++a) um[a] = fma(h, E[a], u[a]);
-    const double rgm = rsqrt(fma(um[0], um[0], fma(um[1], um[1], fma(um[2], um[2], 1.0))));  // 1 / gamma^-
-    const double gg = h * rgm;
-    for (int a = 0; a < 3; ++a) t[a] = gg * B[a];
-    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-    const double k = 2.0 / (1.0 + t2);
-    for (int a = 0; a < 3; ++a) s[a] = k * t[a];
-    double umxt[3];
-    cross(um, t, umxt);
-    for (int a = 0; a < 3; ++a) up[a] = um[a] + umxt[a];
+// Boris step u -> un (half electric kick, rotation, half kick) with the
+// intermediates its adjoint reuses: um = u + h E, rgm = 1/gamma^-, t = h rgm B,
+// k = 2/(1 + t.t), s = k t, up = um + um x t.  The differentiable path's
+// forward step and its adjoint both call it, so they see the same trajectory.
+struct BorisFwd {
+    double um[3], rgm, gg, t[3], k, s[3], up[3];
+};
+
+__device__ __forceinline__ void boris_fwd(const double u[3], const double E[3], const double B[3], double h,
+                                          double un[3], BorisFwd& f) {
+    for (int a = 0; a < 3; ++a) f.um[a] = fma(h, E[a], u[a]);
+    f.rgm = rsqrt_ge1(fma(f.um[0], f.um[0], fma(f.um[1], f.um[1], fma(f.um[2], f.um[2], 1.0))));
+    f.gg = h * f.rgm;
+    for (int a = 0; a < 3; ++a) f.t[a] = f.gg * B[a];
+    f.k = 2.0 * rcp_ge1(1.0 + fma(f.t[0], f.t[0], fma(f.t[1], f.t[1], f.t[2] * f.t[2])));
+    for (int a = 0; a < 3; ++a) f.s[a] = f.k * f.t[a];
+    f.up[0] = fma(f.um[1], f.t[2], fma(-f.um[2], f.t[1], f.um[0]));
+    f.up[1] = fma(f.um[2], f.t[0], fma(-f.um[0], f.t[2], f.um[1]));
+    f.up[2] = fma(f.um[0], f.t[1], fma(-f.um[1], f.t[0], f.um[2]));
+    un[0] = fma(h, E[0], fma(f.up[1], f.s[2], fma(-f.up[2], f.s[1], f.um[0])));
+    un[1] = fma(h, E[1], fma(f.up[2], f.s[0], fma(-f.up[0], f.s[2], f.um[1])));
+    un[2] = fma(h, E[2], fma(f.up[0], f.s[1], fma(-f.up[1], f.s[0], f.um[2])));
+}
+
+// Reverse mode of the Boris step from its forward intermediates: given lun
+// (cotangent of the new u), returns lu (old u) and adds the cotangents of the
+// particle fields into lE, lB.
+__device__ void boris_adjoint(const BorisFwd& f, const double B[3], double h, const double lun[3], double lu[3],
+                              double lE[3], double lB[3]) {
     // un = upl + h E ; upl = um + up x s
     double lum[3], lup[3], ls[3], lt[3], tmp[3];
     for (int a = 0; a < 3; ++a) {
         lE[a] += h * lun[a];
         lum[a] = lun[a];
     }
-    cross(s, lun, lup);  // lambda_up = s x lambda_upl
-    cross(lun, up, ls);  // lambda_s = lambda_upl x up
+    cross(f.s, lun, lup);  // lambda_up = s x lambda_upl
+    cross(lun, f.up, ls);  // lambda_s = lambda_upl x up
     // up = um + um x t
-    cross(t, lup, tmp);
+    cross(f.t, lup, tmp);
     for (int a = 0; a < 3; ++a) lum[a] += lup[a] + tmp[a];
-    cross(lup, um, lt);  // lambda_t = lambda_up x um
+    cross(lup, f.um, lt);  // lambda_t = lambda_up x um
     // s = k t, k = 2 / (1 + t.t)
-    const double lk = ls[0] * t[0] + ls[1] * t[1] + ls[2] * t[2];
-    const double lt2 = -0.5 * k * k * lk;
-    for (int a = 0; a < 3; ++a) lt[a] += k * ls[a] + 2.0 * t[a] * lt2;
-    // t = g B, g = h / gm, gm = sqrt(1 + um.um)
+    const double lk = ls[0] * f.t[0] + ls[1] * f.t[1] + ls[2] * f.t[2];
+    const double lt2 = -0.5 * f.k * f.k * lk;
+    for (int a = 0; a < 3; ++a) lt[a] += f.k * ls[a] + 2.0 * f.t[a] * lt2;
+    // t = g B, g = h / gamma^-, gamma^- = sqrt(1 + um.um)
     const double lg = lt[0] * B[0] + lt[1] * B[1] + lt[2] * B[2];
-    for (int a = 0; a < 3; ++a) lB[a] += gg * lt[a];
+    for (int a = 0; a < 3; ++a) lB[a] += f.gg * lt[a];
     // d gamma^- / d um = um / gamma^-, d g / d gamma^- = -g / gamma^-
-    const double lgm = -lg * gg * rgm;
-    for (int a = 0; a < 3; ++a) lum[a] += (lgm * rgm) * um[a];
+    const double lgm = -lg * f.gg * f.rgm;
+    for (int a = 0; a < 3; ++a) lum[a] += (lgm * f.rgm) * f.um[a];
     // um = u + h E
     for (int a = 0; a < 3; ++a) {
         lu[a] = lum[a];
@@ -265,11 +264,8 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
                 cell[c] = cell0[c] + o;
                 pa[c] -= o;
             }
-            double m[3], om[3];
-            for (int c = 0; c < 3; ++c) {
-                m[c] = fma(0.5, dd[c], pa[c]);
-                om[c] = 1.0 - m[c];
-            }
+            double m[3];
+            for (int c = 0; c < 3; ++c) m[c] = fma(0.5, dd[c], pa[c]);
             double lpa[3] = {0, 0, 0}, ldd[3] = {0, 0, 0};
             for (int c = 0; c < 3; ++c) {
                 const int p = (c + 1) % 3, r = (c + 2) % 3;
@@ -283,12 +279,15 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
                         idx[r] += s2;
                         L[s1][s2] = Lc[pidx(g, idx[0], idx[1], idx[2])];
                     }
-                // f = Q d_c [Sum L W_p W_r + K d_p d_r / 12]
-                const double S = L[0][0] * om[p] * om[r] + L[1][0] * m[p] * om[r] + L[0][1] * om[p] * m[r] +
-                                 L[1][1] * m[p] * m[r];
-                const double K = L[0][0] - L[1][0] - L[0][1] + L[1][1];
-                const double Dp = -L[0][0] * om[r] + L[1][0] * om[r] - L[0][1] * m[r] + L[1][1] * m[r];
-                const double Dr = -L[0][0] * om[p] - L[1][0] * m[p] + L[0][1] * om[p] + L[1][1] * m[p];
+                // f = Q d_c [Sum L W_p W_r + K d_p d_r / 12]: S = Sum L W_p W_r is the
+                // bilinear interpolant of the four edge cotangents at (m_p, m_r),
+                // Dp, Dr its slopes and K its cross slope
+                const double a0 = L[1][0] - L[0][0], a1 = L[1][1] - L[0][1];
+                const double K = a1 - a0;
+                const double Sp0 = fma(m[p], a0, L[0][0]), Sp1 = fma(m[p], a1, L[0][1]);
+                const double Dr = Sp1 - Sp0;
+                const double S = fma(m[r], Dr, Sp0);
+                const double Dp = fma(m[r], K, a0);
                 const double qd = Q[c] * dd[c];
                 ldd[c] += Q[c] * (S + K * dd[p] * dd[r] * (1.0 / 12.0));
                 lpa[p] += qd * Dp;
@@ -312,8 +311,9 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
     // t = (face - a_ax) / d_ax
     for (int s = 0; s + 1 < P.n; ++s) {
         const int c = P.ax[s];
-        la[c] -= lt[s] / d[c];
-        ld[c] -= lt[s] * P.t[s] / d[c];
+        const double q = lt[s] / d[c];
+        la[c] -= q;
+        ld[c] -= q * P.t[s];
     }
 }
 
@@ -335,8 +335,12 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, S
         corners(EB, g, c, base, v);
         F[c] = tri_val(v, f);
     }
-    boris(u, F, F + 3, sp.qdt2m);
-    const double gi = rsqrt(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
+    {
+        BorisFwd bf;
+        const double u0[3] = {u[0], u[1], u[2]};
+        boris_fwd(u0, F, F + 3, sp.qdt2m, u, bf);
+    }
+    const double gi = rsqrt_ge1(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
     double d[3], a[3];
     int cell0[3];
     for (int c = 0; c < 3; ++c) {
@@ -411,10 +415,11 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
         dF[c][0] = fma(f[2], b1 - b0, b0);
         F[c] = fma(f[2], dF[c][2], c0);
     }
-    double u1[3] = {u0[0], u0[1], u0[2]};
-    boris(u1, F, F + 3, sp.qdt2m);
+    double u1[3];
+    BorisFwd bf;
+    boris_fwd(u0, F, F + 3, sp.qdt2m, u1, bf);
     const double u2p1 = fma(u1[0], u1[0], fma(u1[1], u1[1], fma(u1[2], u1[2], 1.0)));
-    const double gi = rsqrt(u2p1);
+    const double gi = rsqrt_ge1(u2p1);
     double d[3], a[3];
     int cell0[3];
     for (int c = 0; c < 3; ++c) {
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     for (int c = 0; c < 3; ++c) lu1[c] += ldv[c] * gi - u1[c] * dot * gi3;
     // Boris
     double lu0[3], lF[6] = {0, 0, 0, 0, 0, 0};
-    boris_adjoint(u0, F, F + 3, sp.qdt2m, lu1, lu0, lF, lF + 3);
+    boris_adjoint(bf, F + 3, sp.qdt2m, lu1, lu0, lF, lF + 3);
     // gather: scatter lambda_F with the separable CIC weights, and the position gradient
     for (int c = 0; c < 6; ++c) {
         const double* f = fr[c];

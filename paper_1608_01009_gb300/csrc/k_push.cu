@@ -29,38 +29,6 @@
 
 namespace picgb {
 
-// FP64 reciprocal square root and reciprocal for arguments >= 1 (the Lorentz
-// factors and Boris denominators of the push): the PTX approximations as seeds
-// and one correction from the binomial series, with e = 1 - x y0^2,
-//   1/sqrt(x) = y0 (1 - e)^(-1/2) ~ y0 (1 + e/2 + 3 e^2/8),
-// and with e = 1 - x r0,  1/x = r0 / (1 - e) ~ r0 (1 + e + e^2):
-// third-order convergence, so a seed good to about 2^-22 gives a full FP64
-// result in 4 (rsqrt) and 3 (reciprocal) FP64 operations; both stay within
-// 2.3e-16 relative of CUDA's rsqrt and of IEEE division over [1, 1e8] (c2
-// particle kernel 5.32 -> 5.28 ms).
-#ifndef PICGB_F64_NR
-#define PICGB_F64_NR 1  // 0: CUDA's rsqrt and IEEE division
-#endif
-__device__ __forceinline__ double rsqrt_ge1(double x) {
-#if PICGB_F64_NR
-    double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double e = fma(-x * y, y, 1.0);
-    return fma(y * e, fma(e, 0.375, 0.5), y);
-#else
-    return rsqrt(x);
-#endif
-}
-__device__ __forceinline__ double rcp_ge1(double x) {
-#if PICGB_F64_NR
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    const double e = fma(-x, r, 1.0);
-    return fma(fma(e, e, e), r, r);
-#else
-    return 1.0 / x;
-#endif
-}
 
 // min(v, largest double below 1) for v in [0, 1], on the bit pattern.
 __device__ __forceinline__ double below_one_of(double v) {
