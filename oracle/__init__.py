@@ -16,7 +16,20 @@ import numpy as np
 
 from . import build_oracle
 
-_lib = None
+_libs = {}
+_threads = False
+
+
+def use_threads(on: bool = True):
+    """Route every following oracle call to the threaded timing build (whole
+    steps push the particles on all host cores) or back to the serial build."""
+    global _threads
+    _threads = bool(on)
+
+
+def threads() -> int:
+    """Host threads a whole step of the current build uses."""
+    return int(lib().or_threads())
 
 
 class OrGrid(C.Structure):
@@ -35,9 +48,10 @@ _PP = C.POINTER(_P)
 
 
 def lib():
-    global _lib
+    _lib = _libs.get(_threads)
     if _lib is None:
-        _lib = C.CDLL(build_oracle.build())
+        _lib = C.CDLL(build_oracle.build(threads=_threads))
+        _libs[_threads] = _lib
         G = C.POINTER(OrGrid)
         S = C.POINTER(OrSpecies)
         sig = {
@@ -58,6 +72,8 @@ def lib():
             f = getattr(_lib, name)
             f.argtypes = args
             f.restype = C.c_double if name in ("or_field_energy", "or_kinetic_energy") else None
+        _lib.or_threads.argtypes = []
+        _lib.or_threads.restype = C.c_int
     return _lib
 
 

@@ -40,6 +40,9 @@
 //
 // Build: g++ -O2 -ffp-contract=off -fPIC -shared (oracle/build_oracle.py).
 // -ffp-contract=off keeps every product and sum rounded separately, as written.
+// A second build with -fopenmp (libpic_oracle_threads.so) runs whole steps'
+// particle loop on all host cores; it exists to time the oracle on the host,
+// and the tests check it against the serial build.
 
 #include <cmath>
 #include <cstdint>
@@ -47,6 +50,9 @@
 #include <cstdlib>
 #include <vector>
 #include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -508,12 +514,46 @@ void push_and_deposit(const or_grid& g, T* const E[3], T* const B[3], T* J[3], S
     }
 }
 
+#ifdef _OPENMP
+// Timing build only (build_oracle.py's threaded variant, which times the oracle
+// on all host cores): the particles are split into one contiguous range per
+// thread, each range goes through push_and_deposit above -- the same
+// statements, particle by particle -- into a thread-private current, and the
+// private currents are added into J in thread order.  Only the summation order
+// of J differs from the serial build, which compiles without this.
+template <class T>
+void push_and_deposit_threads(const or_grid& g, T* const E[3], T* const B[3], T* J[3], SpeciesT<T>& sp) {
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int nt = omp_get_max_threads();
+    std::vector<T> priv((size_t)nt * 3 * ncell, T(0.0));
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = omp_get_thread_num();
+        const int64_t a = sp.n * t / nt, b = sp.n * (t + 1) / nt;
+        SpeciesT<T> part = sp;
+        part.n = b - a;
+        part.x += a, part.y += a, part.z += a, part.ux += a, part.uy += a, part.uz += a, part.w += a;
+        part.active += a;
+        T* Jt[3] = {&priv[((size_t)t * 3 + 0) * ncell], &priv[((size_t)t * 3 + 1) * ncell],
+                    &priv[((size_t)t * 3 + 2) * ncell]};
+        push_and_deposit(g, E, B, Jt, part);
+    }
+    for (int t = 0; t < nt; ++t)
+        for (int c = 0; c < 3; ++c)
+            for (long long o = 0; o < ncell; ++o) J[c][o] += priv[((size_t)t * 3 + c) * ncell + o];
+}
+#endif
+
 template <class T>
 void step(const or_grid& g, T* E[3], T* B[3], T* J[3], std::vector<SpeciesT<T>>& sps) {
     long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
     for (int c = 0; c < 3; ++c)
         for (long long o = 0; o < ncell; ++o) J[c][o] = T(0.0);
+#ifdef _OPENMP
+    for (auto& sp : sps) push_and_deposit_threads(g, E, B, J, sp);
+#else
     for (auto& sp : sps) push_and_deposit(g, E, B, J, sp);
+#endif
     fdtd_b_half(g, E, B);
     fdtd_e(g, E, B, J);
     fdtd_b_half(g, E, B);
@@ -624,6 +664,15 @@ void or_push_deposit(const or_grid* g, double* const* E, double* const* B, doubl
     double* Jp[3] = {J[0], J[1], J[2]};
     SpeciesT<double> s = as_double(*sp);
     push_and_deposit(*g, E, B, Jp, s);
+}
+
+// Host threads the particle loop of a whole step uses (1 in the serial build).
+int or_threads() {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 double or_field_energy(const or_grid* g, double* const* E, double* const* B) {

@@ -472,3 +472,26 @@ def test_work_energy_theorem_uniform_e():
     sp = ora.species[0]
     sp.w[0] = 2.5
     assert abs(ora.kinetic_energy() - 2.5 * (g - 1.0)) < 1e-14
+
+
+# ---------------------------------------------------------------- threaded timing build
+def test_threaded_timing_build_matches_the_serial_oracle():
+    # the threaded build (used only to time the oracle on all host cores) runs the
+    # same per-particle statements on contiguous particle ranges into private
+    # currents; only J's summation order differs, so one step agrees to rounding
+    from paper_1608_01009_gb300 import workloads as W
+    wl = W.config("c1")
+    O.use_threads(False)
+    a = O.Oracle.from_workload(wl.copy())
+    a.step(1)
+    O.use_threads(True)
+    try:
+        assert O.threads() >= 1
+        b = O.Oracle.from_workload(wl.copy())
+        b.step(1)
+    finally:
+        O.use_threads(False)
+    for F, G in ((a.E, b.E), (a.B, b.B), (a.J, b.J)):
+        assert np.max(np.abs(F - G)) <= 1e-15 * np.max(np.abs(F))
+    for k in range(6):
+        assert np.array_equal(a.species[0].arr[k], b.species[0].arr[k]), k  # particles: identical statements
