@@ -65,9 +65,14 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+KERNEL_SOURCES = {"fp64": ("k_push.cu", "push_tile.cuh", "pic_internal.cuh"),
+                  "mixed": ("k_push32.cu", "push_tile.cuh", "pic_internal.cuh"),
+                  "tsc": ("k_tsc.cu", "pic_internal.cuh")}
+
+
 def _kernel_hash(kind="fp64"):
     h = hashlib.sha256()
-    for f in ("k_tsc.cu" if kind == "tsc" else "k_push.cu", "pic_internal.cuh"):
+    for f in KERNEL_SOURCES[kind]:
         with open(os.path.join(ROOT, "paper_1608_01009_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -469,6 +474,17 @@ def run_profile_case(args):
     torch.cuda.set_device(0)
     from paper_1608_01009_gb300 import pic, workloads as W
     ff = 2 if args.profile_case == "tsc" else 1
+    if args.profile_case == "adjoint":
+        # the laser slab c4 (262,144 electrons): a 40-step tape, checkpoint every 20, and its backward
+        sim = pic.Simulation.from_workload(W.config("c4"))
+        t0 = time.perf_counter()
+        sim.tape_forward(40, 20)
+        sim.tape_backward(1.0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "adjoint", "workload": "c4 laser slab, 40-step tape, checkpoint 20",
+                          "seconds": time.perf_counter() - t0}))
+        sim.close()
+        return 0
     if args.profile_case in ("fp64", "tsc"):
         wl, prec = W.config("c2"), "fp64"
     else:
@@ -546,7 +562,8 @@ def run_gpu(args):
                         "ms_per_step": ms3 / args.steps,
                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                      "frac": gbs / hbm_peak, "traffic": _traffic("mixed"),
-                                     "kernel": "k_push<float,4>", "per_launch_ms": pm},
+                                     "kernel": "k_push_g<4> (mixed gather + Boris + move + VB deposit)",
+                                     "per_launch_ms": pm},
                         "stage_ms_per_step": {k: round(v, 4) for k, v in r3["stage_ms"].items()},
                         "gpu_launches": r3["launches"], "clocks": clk3.summary()}
         r3["sim"].close()
@@ -641,10 +658,11 @@ def main():
     ap.add_argument("--no-laser-ramp", action="store_true", help="skip the c5 laser-plasma run and its adjoint")
     ap.add_argument("--laser-ramp", action="store_true",
                     help="run only the 134 M-particle laser-plasma workload with its 50-step adjoint")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed", "tsc"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "tsc", "adjoint"], default=None,
                     help="run only one reduced case for ncu captures (a few GB on the device): "
                          "fp64 = the 64^3 x 50 FP64 plasma, mixed = a 96^3 x 32 mixed plasma, "
-                         "tsc = the 64^3 x 50 plasma with the second-order form factor")
+                         "tsc = the 64^3 x 50 plasma with the second-order form factor, "
+                         "adjoint = a 40-step tape of the laser slab and its backward")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
