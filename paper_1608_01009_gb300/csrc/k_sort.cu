@@ -20,11 +20,12 @@
 //                   the bin starts made global and the tile's part of the
 //                   chunk table the particle kernel walks written (each bin cut
 //                   into near-equal chunks of at most CHUNK particles)
-//   k_sort_scatter: every active particle copied to its slot in the other
-//                   buffer (order inside a cell unspecified); deactivated
-//                   particles are dropped (compaction).  It recomputes each
-//                   key from the cell it copies anyway, so no per-particle
-//                   key array is written or read.
+//   k_sort_scatter_tiled: every active particle copied to its slot in the
+//                   other buffer (order inside a cell unspecified), through a
+//                   shared-memory tile written back in destination order;
+//                   deactivated particles are dropped (compaction).  It
+//                   recomputes each key from the cell it copies anyway, so no
+//                   per-particle key array is written or read.
 #include "pic_internal.cuh"
 
 namespace picgb {
@@ -242,70 +243,12 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_add(int* __restrict__ counts, 
     }
 }
 
-// Records per lane: FP32 (36 B) eight, FP64 (64 B) four.  Each lane loads its
-// whole records before claiming their slots, so the loads overlap the slot
-// atomics (mixed 128^3 x 32 sort per step: 2 records 1.05 ms, 4 0.87 ms,
-// 8 0.84 ms; FP64 64^3 x 50: 2 records 0.167 ms, 4 0.159 ms).
-#ifndef PICGB_SCATTER_U_F32
-#define PICGB_SCATTER_U_F32 8
-#endif
-#ifndef PICGB_SCATTER_U_F64
-#define PICGB_SCATTER_U_F64 4
-#endif
-template <class R>
-struct ScatterU {
-    static constexpr int U = sizeof(R) == 8 ? PICGB_SCATTER_U_F64 : PICGB_SCATTER_U_F32;
-};
-
-template <class R>
-__global__ void __launch_bounds__(SORT_NT) k_sort_scatter(PStore<R> src, PStore<R> dst, const long long* __restrict__ n_cur,
-                                                         GridDev g, int* __restrict__ cursor) {
-    constexpr int U = ScatterU<R>::U;
-    const long long N = *n_cur;
-    const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * SORT_NT * U;
-    for (long long base = ((long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31)) * U; base < N; base += stride) {
-        int key[U], slot[U], cell[U], id[U];
-        R off[U][3], u[U][3], w[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const long long p = base + i * 32 + lane;
-            key[i] = -1;
-            if (p < N) {
-                cell[i] = src.cell[p];
-                key[i] = cell[i] < 0 ? -1 : cell_key(g, cell[i]);  // the count kernel's key, recomputed
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    off[i][a] = src.off[a][p];
-                    u[i][a] = src.u[a][p];
-                }
-                w[i] = src.w[p];
-                id[i] = src.id[p];
-            }
-        }
-        warp_agg_slots<U>(cursor, key, slot);
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const int q = slot[i];
-            if (q >= 0) {
-                dst.cell[q] = cell[i];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    dst.off[a][q] = off[i][a];
-                    dst.u[a][q] = u[i][a];
-                }
-                dst.w[q] = w[i];
-                dst.id[q] = id[i];
-            }
-        }
-    }
-}
-
-// Tiled scatter.  The scatter above writes every cell run in pieces claimed by
-// different warps at different times, and a piece's ends leave 32-byte sectors
-// partly written (DRAM write traffic 31% above the moved bytes, 96^3 x 32
-// FP32 capture).  Here each CTA stages a tile of TR x SORT_NT consecutive
-// records in shared memory:
+// Tiled scatter.  A scatter that claims slots per warp (one global atomic per
+// distinct key and warp) writes every cell run in pieces claimed by different
+// warps at different times, and a piece's ends leave 32-byte sectors partly
+// written (DRAM write traffic 31% above the moved bytes, 96^3 x 32 FP32
+// capture).  Here each CTA stages a tile of TR x SORT_NT consecutive records in
+// shared memory:
 //   * keys inside a window of SW keys around the tile's first key take their
 //     rank within the tile from shared-memory counters (one claim per distinct
 //     key and warp group), the window is scanned, and each key present claims
@@ -318,9 +261,6 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter(PStore<R> src, PStore<
 // particles, against +31% before); mixed 128^3 x 32 sort 0.824 -> 0.724 ms per
 // step with 4 records per thread (8: 0.776, 2: 0.822); FP64 64^3 x 50 0.163
 // -> 0.161 ms with 2 (4: 0.172).
-#ifndef PICGB_SORT_TILED
-#define PICGB_SORT_TILED 1
-#endif
 constexpr int SW = 1024;  // keys per window
 #ifndef PICGB_TILE_TR32
 #define PICGB_TILE_TR32 4
@@ -489,17 +429,13 @@ cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> sr
     k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, tile_nch, ntiles, g.nbins, bin_start, n_next, nchunks);
     k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, tile_nch, ntiles, n_next, kpb, bin_start,
                                            chunks);
-    if (PICGB_SORT_TILED) {
-        const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)TileScatter<R>::SMEM);
-        if (e != cudaSuccess) return e;
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter_tiled<R>, SORT_NT, TileScatter<R>::SMEM);
-        k_sort_scatter_tiled<R><<<nsm * (per_sm > 0 ? per_sm : 1), SORT_NT, TileScatter<R>::SMEM, st>>>(
-            src, dst, n_cur, g, cursor);
-    } else {
-        k_sort_scatter<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, dst, n_cur, g, cursor);
-    }
+    const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)TileScatter<R>::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter_tiled<R>, SORT_NT, TileScatter<R>::SMEM);
+    k_sort_scatter_tiled<R><<<nsm * (per_sm > 0 ? per_sm : 1), SORT_NT, TileScatter<R>::SMEM, st>>>(src, dst, n_cur,
+                                                                                                   g, cursor);
     return cudaGetLastError();
 }
 
