@@ -66,7 +66,8 @@ typedef enum {
     PIC_ERR_NAN = -5,          /* a non-finite value reached the energy diagnostics */
     PIC_ERR_CUDA = -6,         /* a CUDA runtime call failed */
     PIC_ERR_STATE = -7,        /* call not valid in the current state */
-    PIC_ERR_TIMEOUT = -8       /* a bounded wait inside a kernel expired */
+    PIC_ERR_TIMEOUT = -8,      /* a bounded wait inside a kernel expired */
+    PIC_ERR_INDEX = -9         /* debug build only: a kernel index fell outside its array */
 } pic_status;
 
 enum { PIC_BC_PERIODIC = 0, PIC_BC_ABSORBING = 1 };
@@ -317,6 +318,29 @@ PIC_API int pic_set_state(pic_ctx* ctx, const void* blob, int64_t bytes);
  * that flag, so the context stays usable; PIC_ERR_STATE if a device flag was
  * already set before the call.  Synchronises. */
 PIC_API int pic_selftest_wait_timeout(pic_ctx* ctx);
+
+/* Self test of the debug build's index checks (a library facility; the paper
+ * has no counterpart).  The library built with PICGB_DEBUG=1
+ * (libpicgb_debug.so) passes every index its particle, second-order
+ * form-factor, differentiable-path and sort kernels use to address an array
+ * through a check against that array's size; an index outside sets a flag and
+ * the access is skipped, so a wrong index shows as PIC_ERR_INDEX from the next
+ * status read (pic_sync, pic_step) instead of a memory fault.  The flags are
+ * per device and process, not per context.  This call launches a one-thread
+ * kernel on `device` that checks index 1 against an array of one element
+ * (nothing is read or written but the flag), reads that flag and clears it.
+ * Returns PIC_ERR_INDEX in the debug build (the check fired), PIC_OK in the
+ * release build (the checks are compiled out), PIC_ERR_CUDA on a CUDA error.
+ * Synchronises the device. */
+PIC_API int pic_selftest_index_check(int device);
+
+/* Index-check status of `device` (debug build): after synchronising the
+ * device, PIC_ERR_INDEX if any checking kernel of any context saw an index
+ * outside its array since the last pic_index_status (or context status read,
+ * which also takes the flags), else PIC_OK; the flags are cleared.  The
+ * release build returns PIC_OK (nothing is checked).  PIC_ERR_CUDA if the
+ * device cannot be selected or synchronised. */
+PIC_API int pic_index_status(int device);
 
 /* Field energy W_F = 1/2 dx dy dz sum (E^2 + B^2) of caller-provided fields,
  * allocating nothing.  The paper has no counterpart: this is a library

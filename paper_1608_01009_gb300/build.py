@@ -1,6 +1,9 @@
 """Build libpicgb.so in-tree: every CUDA source compiled for sm_103a, in parallel.
 
-    python -m paper_1608_01009_gb300.build [--force] [--verbose]
+    python -m paper_1608_01009_gb300.build [--force] [--verbose] [--debug]
+
+--debug builds libpicgb_debug.so instead: the same sources with PICGB_DEBUG=1,
+whose kernels check every array index they use (see pic_selftest_index_check).
 """
 import concurrent.futures as cf
 import glob
@@ -12,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpicgb.so")
+LIB_DEBUG = os.path.join(HERE, "libpicgb_debug.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"] + ARCH
@@ -25,15 +29,19 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "pic.h")]
 
 
-def build(force: bool = False, verbose: bool = False, out: str = None, defines=()) -> str:
+def build(force: bool = False, verbose: bool = False, out: str = None, defines=(), debug: bool = False) -> str:
     """Compile every CUDA source for sm_103a into `out` (default: the in-tree
-    libpicgb.so).  `defines` are extra -D macros (launch-shape experiments)."""
-    lib = out or LIB
+    libpicgb.so, or libpicgb_debug.so with `debug`).  `defines` are extra -D
+    macros (launch-shape experiments)."""
+    lib = out or (LIB_DEBUG if debug else LIB)
     if not force and not defines and os.path.exists(lib):
         t = os.path.getmtime(lib)
         if all(os.path.getmtime(p) <= t for p in _deps()):
             return lib
     bdir = BUILD if not defines else BUILD + "_" + "_".join(d.replace("=", "") for d in defines)
+    if debug:
+        defines = tuple(defines) + ("PICGB_DEBUG=1",)
+        bdir = BUILD + "_debug"
     os.makedirs(bdir, exist_ok=True)
     extra = (["-Xptxas", "-v"] if verbose else []) + ["-D" + d for d in defines]
 
@@ -61,4 +69,4 @@ def build(force: bool = False, verbose: bool = False, out: str = None, defines=(
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, debug="--debug" in sys.argv))

@@ -92,7 +92,10 @@ __device__ __forceinline__ double tri_val(const double v[8], const double f[3]) 
 // 8 corner values v[bx + 2 by + 4 bz] of component c around `base`.
 __device__ __forceinline__ void corners(const double* EB, const GridDev& g, int c, const int base[3], double v[8]) {
     const double* F = EB + (long long)c * g.P;
-    for (int q = 0; q < 8; ++q) v[q] = F[pidx(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1), base[2] + (q >> 2))];
+    for (int q = 0; q < 8; ++q) {
+        const long long o = pidx(g, base[0] + (q & 1), base[1] + ((q >> 1) & 1), base[2] + (q >> 2));
+        v[q] = in_range(o, g.P) ? F[o] : 0.0;  // the check is compiled in the debug build only
+    }
 }
 
 __device__ __forceinline__ void cross(const double a[3], const double b[3], double c[3]) {
@@ -237,7 +240,8 @@ __device__ void deposit_global(double* J, const GridDev& g, const int cell0[3], 
                         int idx[3] = {cell[0], cell[1], cell[2]};
                         idx[p] += s1;
                         idx[r] += s2;
-                        atomicAdd(&Jc[pidx(g, idx[0], idx[1], idx[2])], q * fma(sig, k, wp * wr));
+                        const long long o = pidx(g, idx[0], idx[1], idx[2]);
+                        if (in_range(o, g.P)) atomicAdd(&Jc[o], q * fma(sig, k, wp * wr));
                     }
             }
         }
@@ -277,7 +281,8 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
                         int idx[3] = {i0[0], i0[1], i0[2]};
                         idx[p] += s1;
                         idx[r] += s2;
-                        L[s1][s2] = Lc[pidx(g, idx[0], idx[1], idx[2])];
+                        const long long o = pidx(g, idx[0], idx[1], idx[2]);
+                        L[s1][s2] = in_range(o, g.P) ? Lc[o] : 0.0;
                     }
                 // f = Q d_c [Sum L W_p W_r + K d_p d_r / 12]: S = Sum L W_p W_r is the
                 // bilinear interpolant of the four edge cotangents at (m_p, m_r),
@@ -465,6 +470,7 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
         double* S = scat + (long long)c * g.P;
         for (int q = 0; q < 4; ++q) {
             const long long o = pidx(g, bs[c][0], bs[c][1] + (q & 1), bs[c][2] + (q >> 1));
+            if (!in_range(o, g.P - 1)) continue;  // debug build only: o and o + 1
             atomicAdd(&S[o], syz[q] * gx);
             atomicAdd(&S[o + 1], syz[q] * f[0]);
         }
@@ -739,5 +745,7 @@ cudaError_t adj_fold_add_launch(cudaStream_t st, double* L, double* scat, const 
     k_adj_fold_add<<<agrid(g), dim3(AF_BX, AF_BY), 0, st>>>(L, scat, g);
     return cudaGetLastError();
 }
+
+PICGB_INDEX_FLAG_READER(tape_index_flags)
 
 }  // namespace picgb

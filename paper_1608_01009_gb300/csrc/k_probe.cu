@@ -37,9 +37,33 @@ __global__ void __launch_bounds__(PROBE_NT) k_dfma_rate(long long iters, double 
     if (s == -1.25e300) g_probe_sink = s;
 }
 
+// One index outside an array of one element, checked; nothing is addressed.
+__global__ void k_index_probe(int* ok) {
+    const bool inside = in_range(0, 1), outside = in_range(1, 1);
+    if (!inside && outside) *ok = 0;  // never: in_range(0, 1) holds in every build
+}
+
+PICGB_INDEX_FLAG_READER(probe_index_flags)
+
 }  // namespace picgb
 
 using namespace picgb;
+
+extern "C" PIC_API int pic_selftest_index_check(int device) {
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return PIC_ERR_CUDA;
+    }
+    probe_index_flags();  // clear
+    k_index_probe<<<1, 1>>>(nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "pic_selftest_index_check: %s\n", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    return (probe_index_flags() & ERRBIT_INDEX) ? PIC_ERR_INDEX : PIC_OK;
+}
 
 extern "C" PIC_API int pic_probe_fp64_fma(int device, int64_t iters, double* tflops, double* ms) {
     if (!tflops || !ms || iters < 1 || iters > (1LL << 30)) {

@@ -77,6 +77,13 @@ __device__ __forceinline__ int value_offset(int m) {
     else return edge_offset<TJ>(m);
 }
 
+// Shared-tile atomic add; the debug build checks the index against the tile
+// (12 moments per cell with M, else 3 edge components per cell).
+template <class R, int TJ, bool M>
+__device__ __forceinline__ void tile_add(R* Jt, int idx, R v) {
+    if (in_range(idx, (M ? 12 : 3) * TJ * TJ * TJ)) atomicAdd(Jt + idx, v);
+}
+
 // Per distinct key of the warp: the lanes holding it contribute their v, the
 // rest zeros, one reduce-scatter, 12 owner lanes add the totals to the tile.
 template <class R, int TJ, bool M>
@@ -93,7 +100,7 @@ __device__ __forceinline__ void deposit_by_key(R* Jt, int key, const R (&v)[12])
 #pragma unroll
         for (int i = 0; i < 12; ++i) c[i] = mine ? v[i] : R(0);
         const R t = reduce_scatter12<R>(c);
-        if (owner) atomicAdd(Jt + k + eo, t);
+        if (owner) tile_add<R, TJ, M>(Jt, k + eo, t);
     }
 }
 
@@ -178,7 +185,7 @@ __device__ __forceinline__ void deposit_segment(R* Jt, int key, R ax, R ay, R az
     }
     if (tail && key >= 0) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) atomicAdd(Jt + key + value_offset<M, TJ>(i), v[i]);
+        for (int i = 0; i < 12; ++i) tile_add<R, TJ, M>(Jt, key + value_offset<M, TJ>(i), v[i]);
     }
 }
 
@@ -191,48 +198,44 @@ __device__ __forceinline__ void piece_direct(R* Jt, int b, R ax, R ay, R az, R d
     const R mx = fma(h, dx, ax), my = fma(h, dy, ay), mz = fma(h, dz, az);
     const R vol = dx * dy * (dz * tw);  // sigma term d_x d_y d_z / 12, shared by the 3 components
     if constexpr (M) {
-        R* J = Jt + b;
         const R qx = Qx * dx, bx = qx * my;
-        atomicAdd(J, qx);
-        atomicAdd(J + TJ3, bx);
-        atomicAdd(J + 2 * TJ3, qx * mz);
-        atomicAdd(J + 3 * TJ3, fma(bx, mz, Qx * vol));
+        tile_add<R, TJ, M>(Jt, b, qx);
+        tile_add<R, TJ, M>(Jt, b + TJ3, bx);
+        tile_add<R, TJ, M>(Jt, b + 2 * TJ3, qx * mz);
+        tile_add<R, TJ, M>(Jt, b + 3 * TJ3, fma(bx, mz, Qx * vol));
         const R qy = Qy * dy, by = qy * mx;
-        atomicAdd(J + 4 * TJ3, qy);
-        atomicAdd(J + 5 * TJ3, by);
-        atomicAdd(J + 6 * TJ3, qy * mz);
-        atomicAdd(J + 7 * TJ3, fma(by, mz, Qy * vol));
+        tile_add<R, TJ, M>(Jt, b + 4 * TJ3, qy);
+        tile_add<R, TJ, M>(Jt, b + 5 * TJ3, by);
+        tile_add<R, TJ, M>(Jt, b + 6 * TJ3, qy * mz);
+        tile_add<R, TJ, M>(Jt, b + 7 * TJ3, fma(by, mz, Qy * vol));
         const R qz = Qz * dz, bz = qz * mx;
-        atomicAdd(J + 8 * TJ3, qz);
-        atomicAdd(J + 9 * TJ3, bz);
-        atomicAdd(J + 10 * TJ3, qz * my);
-        atomicAdd(J + 11 * TJ3, fma(bz, my, Qz * vol));
+        tile_add<R, TJ, M>(Jt, b + 8 * TJ3, qz);
+        tile_add<R, TJ, M>(Jt, b + 9 * TJ3, bz);
+        tile_add<R, TJ, M>(Jt, b + 10 * TJ3, qz * my);
+        tile_add<R, TJ, M>(Jt, b + 11 * TJ3, fma(bz, my, Qz * vol));
         return;
     }
     const R ox = R(1) - mx, oy = R(1) - my, oz = R(1) - mz;
     {
         const R q = Qx * dx, qc = Qx * vol, qo = q * oy, qm = q * my;
-        R* J = Jt + b;
-        atomicAdd(J, fma(qo, oz, qc));
-        atomicAdd(J + TJ, fma(qm, oz, -qc));
-        atomicAdd(J + TJ2, fma(qo, mz, -qc));
-        atomicAdd(J + TJ + TJ2, fma(qm, mz, qc));
+        tile_add<R, TJ, M>(Jt, b, fma(qo, oz, qc));
+        tile_add<R, TJ, M>(Jt, b + TJ, fma(qm, oz, -qc));
+        tile_add<R, TJ, M>(Jt, b + TJ2, fma(qo, mz, -qc));
+        tile_add<R, TJ, M>(Jt, b + TJ + TJ2, fma(qm, mz, qc));
     }
     {
         const R q = Qy * dy, qc = Qy * vol, qo = q * ox, qm = q * mx;
-        R* J = Jt + TJ3 + b;
-        atomicAdd(J, fma(qo, oz, qc));
-        atomicAdd(J + 1, fma(qm, oz, -qc));
-        atomicAdd(J + TJ2, fma(qo, mz, -qc));
-        atomicAdd(J + 1 + TJ2, fma(qm, mz, qc));
+        tile_add<R, TJ, M>(Jt, TJ3 + b, fma(qo, oz, qc));
+        tile_add<R, TJ, M>(Jt, TJ3 + b + 1, fma(qm, oz, -qc));
+        tile_add<R, TJ, M>(Jt, TJ3 + b + TJ2, fma(qo, mz, -qc));
+        tile_add<R, TJ, M>(Jt, TJ3 + b + 1 + TJ2, fma(qm, mz, qc));
     }
     {
         const R q = Qz * dz, qc = Qz * vol, qo = q * ox, qm = q * mx;
-        R* J = Jt + 2 * TJ3 + b;
-        atomicAdd(J, fma(qo, oy, qc));
-        atomicAdd(J + 1, fma(qm, oy, -qc));
-        atomicAdd(J + TJ, fma(qo, my, -qc));
-        atomicAdd(J + 1 + TJ, fma(qm, my, qc));
+        tile_add<R, TJ, M>(Jt, 2 * TJ3 + b, fma(qo, oy, qc));
+        tile_add<R, TJ, M>(Jt, 2 * TJ3 + b + 1, fma(qm, oy, -qc));
+        tile_add<R, TJ, M>(Jt, 2 * TJ3 + b + TJ, fma(qo, my, -qc));
+        tile_add<R, TJ, M>(Jt, 2 * TJ3 + b + 1 + TJ, fma(qm, my, qc));
     }
 }
 
@@ -380,7 +383,7 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
             base = __shfl_sync(FULL, base, first);
             const int slot = base + __popc(cm & ((1u << lane) - 1u));
             if (cross && slot >= CHUNK) atomicOr(err, ERRBIT_DRIFT);  // a chunk longer than CHUNK: dropped
-            if (cross && slot < CHUNK) {
+            if (cross && slot < CHUNK && in_range(qbase + slot, (long long)gridDim.x * CHUNK)) {
                 const int q = qbase + slot;
                 xq.key[q] = key0;
                 xq.a[0][q] = fx;
@@ -497,6 +500,7 @@ __global__ void __launch_bounds__(NT, 2) k_push(const __grid_constant__ CUtensor
         const int nq = min(s_qn, CHUNK);
         for (int i = threadIdx.x; i < nq; i += NT) {
             const int q = qbase + i;
+            if (!in_range(q, (long long)gridDim.x * CHUNK)) continue;  // debug build only
             const R w = xq.w[q];
             split_direct<R, TJ, kMom>(Jt, xq.key[q], xq.a[0][q], xq.a[1][q], xq.a[2][q], xq.d[0][q], xq.d[1][q],
                                       xq.d[2][q], pp.cq[0] * w, pp.cq[1] * w, pp.cq[2] * w);
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(NT, 2) k_push(const __grid_constant__ CUtensor
             if (v != R(0)) {
                 const long long o = (long long)comp * g.P + (c0x + 1 + tx) +
                                     (long long)g.np[0] * ((c0y + 1 + ty) + (long long)g.np[1] * (c0z + 1 + tz));
-                atomicAdd(&J[o], (double)v);
+                if (in_range(o, 3 * g.P)) atomicAdd(&J[o], (double)v);
             }
         }
         __syncthreads();
@@ -579,5 +583,7 @@ cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const 
 PICGB_PUSH_INST(double, 2)
 PICGB_PUSH_INST(double, 4)
 PICGB_PUSH_INST(double, 8)
+
+PICGB_INDEX_FLAG_READER(push_index_flags)
 
 }  // namespace picgb

@@ -138,10 +138,14 @@ __device__ __forceinline__ void add12i(int* Ji, int key, const float (&a)[12], f
         int hi[2], lo[2];
         fx_split2(a[i], a[i + 1], s, hi, lo);
         const int o0 = key + edge_offset<TJ>(i), o1 = key + edge_offset<TJ>(i + 1);
-        atomicAdd(Ji + o0, hi[0]);
-        atomicAdd(Ji + o1, hi[1]);
-        atomicAdd(Ji + LO + o0, lo[0]);
-        atomicAdd(Ji + LO + o1, lo[1]);
+        if (in_range(o0, LO)) {  // debug build only: the hi and lo halves of one tile copy
+            atomicAdd(Ji + o0, hi[0]);
+            atomicAdd(Ji + LO + o0, lo[0]);
+        }
+        if (in_range(o1, LO)) {
+            atomicAdd(Ji + o1, hi[1]);
+            atomicAdd(Ji + LO + o1, lo[1]);
+        }
     }
 }
 
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                     base = __shfl_sync(FULL, base, first);
                     const int slot = base + __popc(cm & ((1u << lane) - 1u));
                     if (cross && slot >= CHUNK) bad = true;
-                    if (cross && slot < CHUNK) {
+                    if (cross && slot < CHUNK && in_range(qbase + slot, (long long)gridDim.x * CHUNK)) {
                         const int q = qbase + slot;
                         xq.key[q] = key0;
                         xq.a[0][q] = fx;
@@ -465,6 +469,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         const int nq = min(s_qn, CHUNK);
         for (int i = threadIdx.x; i < nq; i += NT) {
             const int q = qbase + i;
+            if (!in_range(q, (long long)gridDim.x * CHUNK)) continue;  // debug build only
             const float w = xq.w[q];
             split_fx<TJ>(Ji, xq.key[q], xq.a[0][q], xq.a[1][q], xq.a[2][q], xq.d[0][q], xq.d[1][q], xq.d[2][q],
                          cqx * w, cqy * w, cqz * w, fxs);
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                 const int tz = r / (TJ * TJ), ty = (r / TJ) % TJ, tx = r % TJ;
                 const long long o = (long long)comp * g.P + (c0x + 1 + tx) +
                                     (long long)g.np[0] * ((c0y + 1 + ty) + (long long)g.np[1] * (c0z + 1 + tz));
-                atomicAdd(&J[o], (double)(((long long)hi << FX_LO_BITS) + lo) * fxinv);
+                if (in_range(o, 3 * g.P)) atomicAdd(&J[o], (double)(((long long)hi << FX_LO_BITS) + lo) * fxinv);
             }
         }
         __syncthreads();
@@ -535,5 +540,7 @@ cudaError_t push32_launch(int grid, cudaStream_t st, const CUtensorMap& tm, cons
                                           double*, double*, int*);
 PICGB_PUSH32_INST(4)
 PICGB_PUSH32_INST(8)
+
+PICGB_INDEX_FLAG_READER(push32_index_flags)
 
 }  // namespace picgb

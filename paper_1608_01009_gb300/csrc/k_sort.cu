@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long
             const long long p = base + i * 32 + lane;
             const int cp = p < N ? ps.cell[p] : INACTIVE;
             key[i] = cp < 0 ? -1 : cell_key(g, cp);
+            if (key[i] >= 0 && !in_range(key[i], (long long)g.n[0] * g.n[1] * g.n[2])) key[i] = -1;  // debug build only
         }
         warp_agg_slots<COUNT_U>(counts, key, slot);
     }
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
             if (p < N) {
                 cell[i] = src.cell[p];
                 key[i] = cell[i] < 0 ? -1 : cell_key(g, cell[i]);
+                if (key[i] >= 0 && !in_range(key[i], (long long)g.n[0] * g.n[1] * g.n[2])) key[i] = -1;  // debug only
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     off[i][a] = src.off[a][p];
@@ -359,7 +361,8 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
             for (int j = 0; j < PER; ++j) {
                 const int k = threadIdx.x * PER + j;
                 s_cnt[k] = run;
-                s_gb[k] = c[j] ? atomicAdd(&cursor[kb + k], c[j]) : 0;
+                s_gb[k] = c[j] && in_range(kb + k, (long long)g.n[0] * g.n[1] * g.n[2]) ? atomicAdd(&cursor[kb + k], c[j])
+                                                                                       : 0;
                 run += c[j];
             }
             if (threadIdx.x == 0) s_nw = total;
@@ -371,6 +374,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
             if (key[i] < 0) continue;
             if (key[i] >= kb && key[i] < kb + SW) {
                 const int tp = s_cnt[key[i] - kb] + rank[i];
+                if (!in_range(tp, TILE)) continue;  // debug build only
                 s_slot[tp] = s_gb[key[i] - kb] + rank[i];
                 s_cell[tp] = cell[i];
 #pragma unroll
@@ -382,6 +386,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
                 s_id[tp] = id[i];
             } else {
                 const int q = rank[i];
+                if (!in_range(q, N)) continue;  // debug build only
                 dst.cell[q] = cell[i];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -396,6 +401,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
         const int nw = s_nw;
         for (int tp = threadIdx.x; tp < nw; tp += SORT_NT) {
             const int q = s_slot[tp];
+            if (!in_range(q, N)) continue;  // debug build only
             dst.cell[q] = s_cell[tp];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -443,5 +449,7 @@ template cudaError_t sort_launch<double>(cudaStream_t, int, const GridDev&, PSto
                                          const long long*, long long*, int*, int*, int*, int*, Chunk*, int*);
 template cudaError_t sort_launch<float>(cudaStream_t, int, const GridDev&, PStore<float>, PStore<float>,
                                         const long long*, long long*, int*, int*, int*, int*, Chunk*, int*);
+
+PICGB_INDEX_FLAG_READER(sort_index_flags)
 
 }  // namespace picgb

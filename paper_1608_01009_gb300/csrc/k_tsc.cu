@@ -65,8 +65,10 @@ __device__ __forceinline__ double interp27(const double* __restrict__ F, const G
         double sy = 0.0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const double* row =
-                F + (ix - 1 + PAD) + (long long)g.np[0] * ((iy - 1 + b + PAD) + (long long)g.np[1] * (iz - 1 + c + PAD));
+            const long long r0 =
+                (ix - 1 + PAD) + (long long)g.np[0] * ((iy - 1 + b + PAD) + (long long)g.np[1] * (iz - 1 + c + PAD));
+            if (!in_range(r0, g.P - 2)) continue;  // debug build only: the row's 3 points in the component
+            const double* row = F + r0;
             const double sx = fma(wx[2], row[2], fma(wx[1], row[1], wx[0] * row[0]));
             sy = fma(wy[b], sx, sy);
         }
@@ -86,7 +88,8 @@ __device__ __forceinline__ void add_current(double* __restrict__ Jc, const GridD
             ijk[a] += ijk[a] < 0 ? g.n[a] : -g.n[a];
         }
     }
-    atomicAdd(Jc + (ijk[0] + PAD) + (long long)g.np[0] * ((ijk[1] + PAD) + (long long)g.np[1] * (ijk[2] + PAD)), v);
+    const long long o = (ijk[0] + PAD) + (long long)g.np[0] * ((ijk[1] + PAD) + (long long)g.np[1] * (ijk[2] + PAD));
+    if (in_range(o, g.P)) atomicAdd(Jc + o, v);
 }
 
 // Esirkepov current of component C.  Window index k of every axis a is the
@@ -243,5 +246,7 @@ cudaError_t tsc_launch(int grid, cudaStream_t st, const PushParams& pp, const PS
     k_push_tsc<<<grid, TSC_NT, 0, st>>>(ps, n_cur, pp, EB, J, ek_part);
     return cudaGetLastError();
 }
+
+PICGB_INDEX_FLAG_READER(tsc_index_flags)
 
 }  // namespace picgb

@@ -616,6 +616,18 @@ int device_status(pic_ctx* c) {
     int flags = 0;
     CUDA_TRY(c, cudaMemcpyAsync(&flags, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
+#if PICGB_DEBUG
+    // the index flags of the checking units, kept sticky in this context's flag word
+    const int idx = push_index_flags() | push32_index_flags() | tsc_index_flags() | tape_index_flags() |
+                    sort_index_flags();
+    if (idx && !(flags & ERRBIT_INDEX)) {
+        flags |= ERRBIT_INDEX;
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_err, &flags, sizeof(int), cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    }
+#endif
+    if (flags & ERRBIT_INDEX)
+        return fail(c, PIC_ERR_INDEX, "a kernel index fell outside its array (debug build check; the access was skipped)");
     if (flags & ERRBIT_TIMEOUT) return fail(c, PIC_ERR_TIMEOUT, "a bounded TMA/mbarrier wait expired in a kernel");
     if (flags & ERRBIT_DRIFT)
         return fail(c, PIC_ERR_BIN_OVERFLOW, "a particle left its supercell slack between sorts");
@@ -1566,6 +1578,20 @@ int pic_selftest_wait_timeout(pic_ctx* c) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     return r;
+}
+
+int pic_index_status(int device) {
+    if (cudaSetDevice(device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return PIC_ERR_CUDA;
+    }
+#if PICGB_DEBUG
+    const int idx = push_index_flags() | push32_index_flags() | tsc_index_flags() | tape_index_flags() |
+                    sort_index_flags();
+    return idx ? PIC_ERR_INDEX : PIC_OK;
+#else
+    return PIC_OK;
+#endif
 }
 
 int pic_tape_forward(pic_ctx* c, int nsteps, int ckpt_every, double* wk) {

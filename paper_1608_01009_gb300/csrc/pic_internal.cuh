@@ -26,7 +26,51 @@ constexpr int PAD = 2;
 constexpr int MAX_SPECIES = 8;
 
 // Sticky device error bits (the host maps them to pic_status codes).
-enum : int { ERRBIT_DRIFT = 1, ERRBIT_TIMEOUT = 2, ERRBIT_NAN = 4 };
+enum : int { ERRBIT_DRIFT = 1, ERRBIT_TIMEOUT = 2, ERRBIT_NAN = 4, ERRBIT_INDEX = 8 };
+
+// Index checks of the debug build (PICGB_DEBUG=1, libpicgb_debug.so; a stand-in
+// for a memory checker).  The particle kernels, the second-order form factor's
+// kernel, the differentiable path's kernels and the sort's scatter pass every
+// index they read or write through in_range(i, n) against the size of the array
+// it addresses; an index outside sets ERRBIT_INDEX in the flag of its
+// translation unit (each unit has its own copy of g_index_err, read and cleared
+// by the host function PICGB_INDEX_FLAG_READER defines there) and the access is
+// skipped.  Release builds compile every check to `true`.
+#ifndef PICGB_DEBUG
+#define PICGB_DEBUG 0
+#endif
+#if PICGB_DEBUG
+static __device__ int g_index_err;
+#endif
+__device__ __forceinline__ bool in_range(long long i, long long n) {
+#if PICGB_DEBUG
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_index_err, ERRBIT_INDEX);
+    return false;
+#else
+    (void)i;
+    (void)n;
+    return true;
+#endif
+}
+#if PICGB_DEBUG
+#define PICGB_INDEX_FLAG_READER(fn)                                  \
+    int fn() {                                                       \
+        int v = 0, zero = 0;                                         \
+        if (cudaMemcpyFromSymbol(&v, g_index_err, sizeof v) != cudaSuccess) return ERRBIT_INDEX; \
+        cudaMemcpyToSymbol(g_index_err, &zero, sizeof zero);         \
+        return v;                                                    \
+    }
+#else
+#define PICGB_INDEX_FLAG_READER(fn) \
+    int fn() { return 0; }
+#endif
+// readers of the units that check (the host ORs them into the sticky status)
+int push_index_flags();
+int push32_index_flags();
+int tsc_index_flags();
+int tape_index_flags();
+int sort_index_flags();
 
 constexpr int INACTIVE = (int)0x80000000;
 

@@ -61,6 +61,7 @@ __device__ __forceinline__ double bil(const Coef<double>& q, double a, double b)
 
 template <class R, int T>
 __device__ __forceinline__ R tri_raw(const R* __restrict__ F, int i, int j, int k, R a, R b, R c) {
+    if (!in_range((k * T + j) * T + i, T * T * T - T * T - T - 1)) return R(0);  // debug build only
     const R* q = F + (k * T + j) * T + i;
     R c00 = lerp(q[0], q[1], a);
     R c10 = lerp(q[T], q[T + 1], a);
@@ -72,6 +73,7 @@ __device__ __forceinline__ R tri_raw(const R* __restrict__ F, int i, int j, int 
 template <class R, int T>
 __device__ __forceinline__ R tri_coef(const Coef<R>* __restrict__ X, int i, int j, int k, R a, R b, R c) {
     const int o = (k * (T - 1) + j) * (T - 1) + i;
+    if (!in_range(o, (T - 1) * (T - 1) * (T - 1))) return R(0);  // debug build only: o + (T-1)^2 < (T-1)^2 T
     const R v0 = bil(X[o], a, b), v1 = bil(X[o + (T - 1) * (T - 1)], a, b);
     return lerp(v0, v1, c);
 }

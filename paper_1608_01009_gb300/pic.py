@@ -16,10 +16,13 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpicgb.so")
+# the debug build, whose kernels check every array index (PICGB_DEBUG=1)
+DEBUG_LIB_PATH = os.path.join(HERE, "libpicgb_debug.so")
 
 PIC_OK = 0
 STATUS = {0: "PIC_OK", -1: "PIC_ERR_ARG", -2: "PIC_ERR_CFL", -3: "PIC_ERR_OOM", -4: "PIC_ERR_BIN_OVERFLOW",
-          -5: "PIC_ERR_NAN", -6: "PIC_ERR_CUDA", -7: "PIC_ERR_STATE", -8: "PIC_ERR_TIMEOUT"}
+          -5: "PIC_ERR_NAN", -6: "PIC_ERR_CUDA", -7: "PIC_ERR_STATE", -8: "PIC_ERR_TIMEOUT",
+          -9: "PIC_ERR_INDEX"}
 FP64, MIXED = 0, 1
 PERIODIC, ABSORBING = 0, 1
 
@@ -82,6 +85,8 @@ SIGNATURES = {
     "pic_tape_backward": [_VP, C.c_double, _VP, _VP, _VP, _VP],
     "pic_tape_particle_grad": [_VP, C.c_int, _VP],
     "pic_probe_fp64_fma": [C.c_int, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "pic_selftest_index_check": [C.c_int],
+    "pic_index_status": [C.c_int],
 }
 
 
@@ -96,10 +101,24 @@ def probe_fp64_fma(device: int = 0, iters: int = 2048):
     return tf.value, ms.value
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libpicgb.so (raises if it has not been built)."""
+def selftest_index_check(device: int = 0) -> int:
+    """Status of the index-check self test (pic_selftest_index_check):
+    PIC_ERR_INDEX (-9) in the debug build, PIC_OK (0) in the release build."""
+    return int(load_library().pic_selftest_index_check(int(device)))
+
+
+def index_status(device: int = 0) -> int:
+    """pic_index_status: PIC_ERR_INDEX (-9) if a kernel of the debug build saw
+    an index outside its array since the last read (flags cleared), else 0."""
+    return int(load_library().pic_index_status(int(device)))
+
+
+def load_library(path: str = None):
+    """Load libpicgb.so, or the library PICGB_LIBRARY names (for example the
+    debug build, DEBUG_LIB_PATH); raises if it has not been built."""
     global _lib
     if _lib is None:
+        path = path or os.environ.get("PICGB_LIBRARY") or LIB_PATH
         if not os.path.exists(path):
             raise RuntimeError("libpicgb.so not built: run `python -m paper_1608_01009_gb300.build` "
                                "(the CUDA library is required; there is no CPU fallback)")

@@ -45,6 +45,17 @@ def test_exports_are_only_the_abi(lib):
     assert exported == _declared()
 
 
+def test_debug_build_exports_the_same_abi():
+    """The index-checking build (PICGB_DEBUG=1) compiles for sm_103a and
+    exports exactly the entry points of the header, like the release build."""
+    import subprocess
+    path = B.build(debug=True)
+    assert path == P.DEBUG_LIB_PATH and os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert exported == _declared()
+
+
 def _desc(**kw):
     g = P.GridDesc()
     n = kw.get("n", (16, 16, 16))
