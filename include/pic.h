@@ -90,10 +90,17 @@ enum { PIC_FP64 = 0, PIC_MIXED = 1 };
  *                 the fields and FP32 shared-memory current sums; global current,
  *                 fields and energy diagnostics stay FP64.
  *   supercell     S, cells per supercell edge: 4 or 8 (2 also for PIC_FP64)
- *   sort_interval K, steps between supercell re-sorts; 0 = the largest allowed,
- *                 K * max_a(dt / d_a) < 1 (a particle moves less than one cell
- *                 per step along each axis, and the supercell tiles carry one
- *                 cell of slack)
+ *   sort_interval K, steps between supercell re-sorts, K * max_a(dt / d_a) < 1
+ *                 (a particle moves less than one cell per step along each
+ *                 axis, and the supercell tiles carry one cell of slack).
+ *                 0 = the library's schedule: PIC_FP64 with the cloud-in-cell
+ *                 form factor sorts every step (its particle kernel is fastest
+ *                 on freshly sorted particles); the second-order form factor
+ *                 takes the largest allowed K; PIC_MIXED sorts when the
+ *                 displacement bound requires it: the particle kernel records
+ *                 each step's largest speed v_i, and a sort precedes the next
+ *                 step once (sum_i v_i + 1) dt / d_a could reach one cell on
+ *                 some axis (at most 64 steps between sorts)
  *   form_factor   0 or 1: cloud-in-cell with the Villasenor-Buneman current
  *                 (Sec. 3, the paper's scheme); 2: the second-order
  *                 (triangular-shaped cloud) form factor, quadratic B-spline

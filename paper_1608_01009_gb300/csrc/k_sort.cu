@@ -68,6 +68,22 @@ __device__ __forceinline__ void warp_agg_slots(int* counters, const int (&key)[U
 // Lane-interleaved groups of U x 32 particles per warp and iteration.
 constexpr int COUNT_U = 4;
 
+#ifndef PICGB_SORT_RUNS
+#define PICGB_SORT_RUNS 1
+#endif
+// Runs of equal keys in consecutive lanes (the store is sorted by key up to
+// the particles that changed cell since the last sort): `head` is the first
+// lane of this lane's run and `len` the run's length.  Equal keys in separate
+// runs make separate runs, each claiming its own slots.
+__device__ __forceinline__ void key_run(int key, int lane, int& head, int& len) {
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    const unsigned le = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // lanes 0..lane
+    head = 31 - __clz(heads & le);
+    const unsigned after = heads & ~le;
+    len = (after ? __ffs(after) - 1 : 32) - head;
+}
+
 template <class R>
 __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long long* __restrict__ n_cur, GridDev g,
                                                        int* __restrict__ counts) {
@@ -76,7 +92,7 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long
     const long long stride = (long long)gridDim.x * SORT_NT * COUNT_U;
     for (long long base = ((long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31)) * COUNT_U; base < N;
          base += stride) {
-        int key[COUNT_U], slot[COUNT_U];
+        int key[COUNT_U];
 #pragma unroll
         for (int i = 0; i < COUNT_U; ++i) {
             const long long p = base + i * 32 + lane;
@@ -84,7 +100,17 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long
             key[i] = cp < 0 ? -1 : cell_key(g, cp);
             if (key[i] >= 0 && !in_range(key[i], (long long)g.n[0] * g.n[1] * g.n[2])) key[i] = -1;  // debug build only
         }
+#if PICGB_SORT_RUNS
+#pragma unroll
+        for (int i = 0; i < COUNT_U; ++i) {
+            int head, len;
+            key_run(key[i], lane, head, len);
+            if (lane == head && key[i] >= 0) atomicAdd(&counts[key[i]], len);
+        }
+#else
+        int slot[COUNT_U];
         warp_agg_slots<COUNT_U>(counts, key, slot);
+#endif
     }
 }
 
@@ -415,6 +441,216 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
     }
 }
 
+#ifndef PICGB_SORT_PIPE
+#define PICGB_SORT_PIPE 1
+#endif
+#ifndef PICGB_PIPE_TILE32
+#define PICGB_PIPE_TILE32 1024
+#endif
+#ifndef PICGB_PIPE_TILE64
+#define PICGB_PIPE_TILE64 256
+#endif
+#ifndef PICGB_PIPE_NT
+#define PICGB_PIPE_NT 256
+#endif
+constexpr int PIPE_NT = PICGB_PIPE_NT;  // threads of the pipelined scatter
+// Pipelined tiled scatter: the same ranking, window scan and one claim per key
+// and tile as k_sort_scatter_tiled, but the tile's records are not held in
+// registers.  Each CTA keeps two tile stages in shared memory, filled by bulk
+// asynchronous copies (one per array) that run while the previous tile is
+// ranked and written: tile t+gridDim loads during tile t.  Records stay in
+// their stage; the window's records are written out through a permutation
+// (s_src: stage position of each destination-ordered slot), so consecutive
+// threads still write consecutive slots of each cell run.
+template <class R>
+struct PipeScatter {
+    static constexpr int TILE = sizeof(R) == 8 ? PICGB_PIPE_TILE64 : PICGB_PIPE_TILE32;  // records per tile
+    static constexpr int TR = TILE / PIPE_NT;
+    static_assert(TR * PIPE_NT == TILE && TILE % 4 == 0, "tile: whole records per thread, 16-byte copies");
+    // stage: 3 offsets, 3 momenta, weight (R), then cell and id (int)
+    static constexpr size_t STAGE = (size_t)TILE * (7 * sizeof(R) + 2 * sizeof(int));
+    // two stages, destination slot and stage position of each ordered record, window counts and claims
+    static constexpr size_t SMEM = 2 * STAGE + (size_t)TILE * 2 * sizeof(int) + 2 * SW * sizeof(int) + 32 * sizeof(int);
+};
+
+template <class R>
+__global__ void __launch_bounds__(PIPE_NT) k_sort_scatter_pipe(PStore<R> src, PStore<R> dst,
+                                                              const long long* __restrict__ n_cur, GridDev g,
+                                                              int* __restrict__ cursor, int* __restrict__ err) {
+    using PS = PipeScatter<R>;
+    constexpr int TILE = PS::TILE, TR = PS::TR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* s_slot = reinterpret_cast<int*>(smem_raw + 2 * PS::STAGE);  // TILE
+    int* s_src = s_slot + TILE;                                        // TILE
+    int* s_cnt = s_src + TILE;                                         // SW: counts, then tile positions
+    int* s_gb = s_cnt + SW;                                            // SW: first slot of each key's claim
+    int* s_scan = s_gb + SW;                                           // 32 warp totals of the block scan
+    __shared__ uint64_t bar[2];
+    __shared__ int s_kb, s_nw;
+    const long long N = *n_cur;
+    const long long ntile = (N + TILE - 1) / TILE;
+    const int lane = threadIdx.x & 31;
+    const auto stR = [&](int st) { return reinterpret_cast<R*>(smem_raw + st * PS::STAGE); };
+    const auto stI = [&](int st) { return reinterpret_cast<int*>(smem_raw + st * PS::STAGE + 7 * TILE * sizeof(R)); };
+    // the copies of tile t into stage st (thread 0): every array of the store is
+    // allocated to a multiple of 4 records, so rounding the last tile's copies
+    // up to 16 bytes stays inside it
+    const auto issue = [&](long long t, int st) {
+        const long long base = t * TILE;
+        const long long nrec = min((long long)TILE, N - base);
+        const uint32_t nR = (uint32_t)((nrec * sizeof(R) + 15) & ~15ll), nI = (uint32_t)((nrec * 4 + 15) & ~15ll);
+        R* sr = stR(st);
+        int* si = stI(st);
+        fence_proxy_async();
+        mbar_expect_tx(&bar[st], 7 * nR + 2 * nI);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bulk_load(sr + a * TILE, src.off[a] + base, nR, &bar[st]);
+            bulk_load(sr + (3 + a) * TILE, src.u[a] + base, nR, &bar[st]);
+        }
+        bulk_load(sr + 6 * TILE, src.w + base, nR, &bar[st]);
+        bulk_load(si, src.cell + base, nI, &bar[st]);
+        bulk_load(si + TILE, src.id + base, nI, &bar[st]);
+    };
+    const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < SW; i += PIPE_NT) s_cnt[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x < ntile) issue(blockIdx.x, 0);
+    uint32_t phase = 0;  // bit st: parity of stage st's next completion
+    int st = 0;
+    for (long long t = blockIdx.x; t < ntile; t += gridDim.x, st ^= 1) {
+        const long long tn = t + gridDim.x;
+        // the other stage was released by the barrier that ended the previous tile
+        if (threadIdx.x == 0 && tn < ntile) issue(tn, st ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[st], (phase >> st) & 1u, WAIT_LIMIT, WAIT_LIMIT_NS);
+        phase ^= 1u << st;
+        if (__syncthreads_or(!ok)) {
+            // leave only once the copy already issued into the other stage has landed
+            if (tn < ntile) mbar_wait_bounded(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u, WAIT_LIMIT, WAIT_LIMIT_NS);
+            if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+            return;
+        }
+        const long long base = t * TILE;
+        const R* sr = stR(st);
+        const int* si = stI(st);
+        // window: from a quarter window below the first active key of the tile's first 32 records
+        if (threadIdx.x < 32) {
+            // the block scan reads 32 warp totals (8 warps write theirs) and leaves its
+            // running total in all 32: cleared for every tile
+            s_scan[threadIdx.x] = 0;
+            const int cp = base + lane < N ? si[lane] : INACTIVE;
+            const unsigned act = __ballot_sync(0xffffffffu, cp >= 0);
+            const int k = cp >= 0 ? cell_key(g, cp) : 0;
+            const int k0 = __shfl_sync(0xffffffffu, k, act ? __ffs(act) - 1 : 0);
+            if (lane == 0) s_kb = act ? max(0, k0 - SW / 4) : 0;
+        }
+        __syncthreads();
+        const int kb = s_kb;
+        int key[TR], rank[TR];
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            const int r = i * PIPE_NT + threadIdx.x;
+            key[i] = -1;
+            if (base + r < N) {
+                const int cp = si[r];
+                key[i] = cp < 0 ? -1 : cell_key(g, cp);
+                if (key[i] >= 0 && !in_range(key[i], nkeys)) key[i] = -1;  // debug build only
+            }
+            const bool inw = key[i] >= kb && key[i] < kb + SW;
+#if PICGB_SORT_RUNS
+            // a run of one key claims its ranks with one atomic: in-window keys from
+            // the shared counters, the others from the global cursor
+            int head, len;
+            key_run(key[i], lane, head, len);
+            int b = 0;
+            if (lane == head) {
+                if (inw) b = atomicAdd(&s_cnt[key[i] - kb], len);
+                else if (key[i] >= 0) b = atomicAdd(&cursor[key[i]], len);
+            }
+            b = __shfl_sync(0xffffffffu, b, head);
+            rank[i] = key[i] >= 0 ? b + lane - head : -1;
+#else
+            // lanes outside the window or without a record form groups of their own
+            const unsigned peers = __match_any_sync(0xffffffffu, inw ? key[i] : -2 - lane);
+            const int leader = __ffs(peers) - 1;
+            int b = 0;
+            if (lane == leader) {
+                if (inw) b = atomicAdd(&s_cnt[key[i] - kb], __popc(peers));
+                else if (key[i] >= 0) b = atomicAdd(&cursor[key[i]], 1);
+            }
+            b = __shfl_sync(0xffffffffu, b, leader);
+            rank[i] = key[i] >= 0 ? b + __popc(peers & ((1u << lane) - 1u)) : -1;
+#endif
+        }
+        __syncthreads();
+        // exclusive scan of the window counts (tile positions); one global claim per key present
+        {
+            constexpr int PER = SW / PIPE_NT;
+            int c[PER], sum = 0;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                c[j] = s_cnt[threadIdx.x * PER + j];
+                sum += c[j];
+            }
+            int total;
+            int run = block_exclusive_scan(sum, s_scan, &total);
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int k = threadIdx.x * PER + j;
+                s_cnt[k] = run;
+                s_gb[k] = c[j] && in_range(kb + k, nkeys) ? atomicAdd(&cursor[kb + k], c[j]) : 0;
+                run += c[j];
+            }
+            if (threadIdx.x == 0) s_nw = total;
+        }
+        __syncthreads();
+        // window records: their destination-ordered position; the others are stored directly
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            if (key[i] < 0) continue;
+            const int r = i * PIPE_NT + threadIdx.x;
+            if (key[i] >= kb && key[i] < kb + SW) {
+                const int tp = s_cnt[key[i] - kb] + rank[i];
+                if (!in_range(tp, TILE)) continue;  // debug build only
+                s_slot[tp] = s_gb[key[i] - kb] + rank[i];
+                s_src[tp] = r;
+            } else {
+                const int q = rank[i];
+                if (!in_range(q, N)) continue;  // debug build only
+                dst.cell[q] = si[r];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    dst.off[a][q] = sr[a * TILE + r];
+                    dst.u[a][q] = sr[(3 + a) * TILE + r];
+                }
+                dst.w[q] = sr[6 * TILE + r];
+                dst.id[q] = si[TILE + r];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < SW; i += PIPE_NT) s_cnt[i] = 0;  // positions read above; counts of the next tile
+        const int nw = in_range(s_nw, TILE + 1) ? s_nw : 0;  // the check: debug build only
+        for (int tp = threadIdx.x; tp < nw; tp += PIPE_NT) {
+            const int q = s_slot[tp], r = s_src[tp];
+            if (!in_range(q, N) || !in_range(r, TILE)) continue;  // debug build only
+            dst.cell[q] = si[r];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dst.off[a][q] = sr[a * TILE + r];
+                dst.u[a][q] = sr[(3 + a) * TILE + r];
+            }
+            dst.w[q] = sr[6 * TILE + r];
+            dst.id[q] = si[TILE + r];
+        }
+        __syncthreads();
+    }
+}
+
 int sort_grid(int nsm) { return nsm * 8; }
 
 long long sort_tiles(long long nkeys) { return (nkeys + SCAN_TILE - 1) / SCAN_TILE; }
@@ -425,7 +661,7 @@ long long sort_tile_scratch(long long nkeys) { return 2 * sort_tiles(nkeys); }
 template <class R>
 cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> src, PStore<R> dst,
                         const long long* n_cur, long long* n_next, int* counts, int* cursor, int* tile_sum,
-                        int* bin_start, Chunk* chunks, int* nchunks) {
+                        int* bin_start, Chunk* chunks, int* nchunks, int* err) {
     const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
     const int ntiles = (int)sort_tiles(nkeys);
     const int kpb = g.S * g.S * g.S;
@@ -435,6 +671,18 @@ cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> sr
     k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, tile_nch, ntiles, g.nbins, bin_start, n_next, nchunks);
     k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, tile_nch, ntiles, n_next, kpb, bin_start,
                                            chunks);
+#if PICGB_SORT_PIPE
+    {
+        constexpr int sm = (int)PipeScatter<R>::SMEM;
+        const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_pipe<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter_pipe<R>, PIPE_NT, sm);
+        k_sort_scatter_pipe<R><<<nsm * (per_sm > 0 ? per_sm : 1), PIPE_NT, sm, st>>>(src, dst, n_cur, g, cursor, err);
+        return cudaGetLastError();
+    }
+#endif
+    (void)err;
     const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)TileScatter<R>::SMEM);
     if (e != cudaSuccess) return e;
@@ -446,9 +694,9 @@ cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> sr
 }
 
 template cudaError_t sort_launch<double>(cudaStream_t, int, const GridDev&, PStore<double>, PStore<double>,
-                                         const long long*, long long*, int*, int*, int*, int*, Chunk*, int*);
+                                         const long long*, long long*, int*, int*, int*, int*, Chunk*, int*, int*);
 template cudaError_t sort_launch<float>(cudaStream_t, int, const GridDev&, PStore<float>, PStore<float>,
-                                        const long long*, long long*, int*, int*, int*, int*, Chunk*, int*);
+                                        const long long*, long long*, int*, int*, int*, int*, Chunk*, int*, int*);
 
 PICGB_INDEX_FLAG_READER(sort_index_flags)
 

@@ -119,6 +119,10 @@ struct PushParams {
     // mixed kernel: the species' largest |w| (device, written by the load), which
     // fixes the scale of the fixed-point current tile
     const float* wmax;
+    // mixed kernel under the displacement-bounded sort schedule: the largest
+    // gamma^2 = 1 + u^2 of this push as float bits (atomicMax; a particle's
+    // displacement is |d_a| = sqrt(1 - 1/gamma^2) dt/d_a); null: not tracked
+    unsigned* drift;
 };
 
 // Per-CTA queue of the moves that leave their start cell (structure of arrays,
@@ -222,6 +226,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         "[%6];" ::"r"(smem_u32(dst)),
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Bulk (non-tensor) copy global -> shared of `bytes` bytes, completion signalled
+// on `bar`: both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 // Budget of a TMA wait: far beyond any legitimate latency (microseconds), short

@@ -93,3 +93,51 @@ def test_mixed_field_energy_after_100_steps():
     assert err_fp64.max() < 1e-9, rec
     # the mixed path's stated target: 1e-5 relative in field energy after 100 steps
     assert err_mixed[99] <= 1e-5, rec
+
+
+def _sorts(sim, steps):
+    # per step: 1 particle kernel + 3 field kernels + 1 energy kernel; 5 per sort
+    return (sim.launch_count() - 5 * steps) // 5
+
+
+def _trajectory_errors(wl, steps, sort_interval=0):
+    import oracle as O
+    sim = PT.make_sim(wl, precision=P.MIXED, sort_interval=sort_interval)
+    ora = O.Oracle.from_workload(wl)
+    sim.launch_count(reset=True)
+    sim.step(steps)
+    sim.sync()  # raises on a particle that left its supercell's slack (PIC_ERR_BIN_OVERFLOW)
+    sorts = _sorts(sim, steps)
+    ora.step(steps)
+    errs = dict(PT.field_errors(sim, ora))
+    errs.update(PT.particle_errors(sim, ora, wl))
+    sim.close()
+    return errs, sorts
+
+
+def test_displacement_bounded_schedule_sorts_less_on_a_thermal_plasma():
+    # vth = 0.1c, dt/d = 0.289: the fixed interval floor(1 / max(dt/d)) = 3 would sort 9
+    # times in 30 steps; the recorded displacements allow longer runs, results unchanged
+    wl = W.uniform_plasma((16, 16, 16), 8, 0.05, 0.1, seed=31, steps=30)
+    errs, sorts = _trajectory_errors(wl, 30)
+    assert sorts <= 7, sorts
+    assert max(errs[k] for k in ("x", "y", "z")) < 1e-5, errs
+    assert max(errs[k] for k in ("ux", "uy", "uz")) < 1e-4, errs
+    errs_k3, sorts_k3 = _trajectory_errors(wl, 30, sort_interval=3)
+    assert sorts_k3 == 9  # before steps 4, 7, ..., 28
+    for k in errs:
+        assert errs[k] <= 10 * errs_k3[k] + 1e-9, (k, errs, errs_k3)
+
+
+def test_displacement_bounded_schedule_keeps_a_relativistic_beam_in_its_tiles():
+    # gamma ~ 8 along x (v = 0.992c): each step moves 0.286 cells, so the schedule must sort
+    # every 3 steps, as the fixed bound does; no particle may leave its slack
+    wl = W.uniform_plasma((16, 8, 8), 4, 0.05, 0.0, seed=32, steps=24)
+    sp = wl.species[0]
+    sp.ux[:] = 8.0
+    sp.uy[:] = 0.3
+    sp.uz[:] = -0.2
+    errs, sorts = _trajectory_errors(wl, 24)
+    assert sorts == 7, sorts  # before steps 4, 7, ..., 22
+    assert max(errs[k] for k in ("x", "y", "z")) < 1e-5, errs
+    assert max(errs[k] for k in ("ux", "uy", "uz")) < 1e-4, errs

@@ -51,7 +51,7 @@ def test_c1_first_step():
 
 def test_c1_after_drift_and_sorts():
     # state after 7 steps: 2 sorts (K = 3) and particles drifted inside their slack
-    _check_one_step(W.config("c1"), warm_steps=7)
+    _check_one_step(W.config("c1"), warm_steps=7, sort_interval=3)
 
 
 @pytest.mark.parametrize("S", [2, 4, 8])
@@ -228,12 +228,20 @@ def test_energy_diagnostics_match_oracle():
 
 def test_status_and_launch_count():
     wl = W.config("c1")
-    sim = PT.make_sim(wl)
+    sim = PT.make_sim(wl, sort_interval=3)
     sim.launch_count(reset=True)
     sim.step(6)
     sim.sync()
     # per step: 1 push + 3 field + 1 energy; one sort (5 kernels) at the 4th step (K = 3)
     assert sim.launch_count() == 6 * 5 + 5
+    sim.close()
+    # the FP64 default sorts before every step after the first (the load sorted)
+    sim = PT.make_sim(wl)
+    sim.launch_count(reset=True)
+    sim.step(6)
+    sim.sync()
+    assert sim.launch_count() == 6 * 5 + 5 * 5
+    sim.close()
 
 
 def test_non_finite_input_is_reported_not_trapped():

@@ -150,7 +150,7 @@ def test_bounded_wait_times_out_and_the_context_recovers():
     sim.close()
 
 
-HEADER = 120  # state blob header bytes (the since_sort counter is its last 8)
+HEADER = 144  # state blob header bytes (the since_sort counter is its last 8)
 
 
 def _cell_offset(wl):
