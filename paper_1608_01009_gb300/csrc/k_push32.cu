@@ -52,9 +52,6 @@ namespace picgb {
 #ifndef PICGB_GM
 #define PICGB_GM 2  // consecutive groups per thread between flushes of its register sums
 #endif
-#ifndef PICGB_PREFETCH
-#define PICGB_PREFETCH 0  // coefficient-tile supercells: the raw tile of the next chunk loads during this one
-#endif
 constexpr int PG = PICGB_PG;  // particles per thread: 2 (8-byte accesses) or 4 (16-byte accesses)
 template <int G>
 struct GVec;
@@ -133,48 +130,9 @@ __device__ __forceinline__ void fx_split2(float v0, float v1, float s, int (&hi)
     lo[1] = __float_as_int(t2.y) - m;
 }
 
-#ifndef PICGB_FX64
-#define PICGB_FX64 0
-#endif
-// Packed form (PICGB_FX64): one 64-bit integer atomic add per value, the high
-// word hi' = round(v s) - 1 and the low word lo = round(r 2^17) + 2^17 in
-// [2^16, 3 2^16] (r = v s - round(v s)), so value = hi' + lo 2^-17.  A 64-bit add
-// of such words sums the low words without a carry into the high word while
-// the low sum stays below 2^32: at most 4 adds per particle reach one address
-// (one per Villasenor-Buneman piece), 4 CHUNK = 2^14 adds of at most 1.5 2^17.
-constexpr int FX64_LO_BITS = 17;
-__device__ __forceinline__ void fx_split2_64(float v0, float v1, float s, unsigned long long (&q)[2]) {
-    const float2 M = make_float2(FX_MAGIC, FX_MAGIC);
-    const float2 x = __fmul2_rn(make_float2(v0, v1), make_float2(s, s));
-    const float2 t = __fadd2_rn(x, M);
-    const float2 d = __fadd2_rn(t, make_float2(-FX_MAGIC, -FX_MAGIC));  // round(x), exact
-    const float2 r = __fadd2_rn(x, make_float2(-d.x, -d.y));            // exact, |r| <= 1/2
-    constexpr float LS = (float)(1 << FX64_LO_BITS), MO = FX_MAGIC + (float)(1 << FX64_LO_BITS);
-    const float2 t2 = __ffma2_rn(r, make_float2(LS, LS), make_float2(MO, MO));
-    const int m = __float_as_int(FX_MAGIC);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const unsigned hi = (unsigned)(__float_as_int(k ? t.y : t.x) - (m + 1));
-        const unsigned lo = (unsigned)(__float_as_int(k ? t2.y : t2.x) - m);
-        q[k] = ((unsigned long long)hi << 32) | lo;
-    }
-}
-
 template <int TJ>
 __device__ __forceinline__ void add12i(int* Ji, int key, const float (&a)[12], float s) {
     constexpr int LO = 3 * TJ * TJ * TJ;
-#if PICGB_FX64
-    unsigned long long* Jq = reinterpret_cast<unsigned long long*>(Ji);
-#pragma unroll
-    for (int i = 0; i < 12; i += 2) {
-        unsigned long long q[2];
-        fx_split2_64(a[i], a[i + 1], s, q);
-        const int o0 = key + edge_offset<TJ>(i), o1 = key + edge_offset<TJ>(i + 1);
-        if (in_range(o0, LO)) atomicAdd(Jq + o0, q[0]);  // debug build only: inside one tile copy
-        if (in_range(o1, LO)) atomicAdd(Jq + o1, q[1]);
-    }
-    return;
-#endif
 #pragma unroll
     for (int i = 0; i < 12; i += 2) {
         int hi[2], lo[2];
@@ -227,12 +185,11 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
              double* __restrict__ ek_part, int* __restrict__ err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
     constexpr bool kCoef = Tile<float, S>::kCoef;
-    constexpr bool kPre = PICGB_PREFETCH && kCoef;  // raw tile, J tile and coefficients in separate regions
-    constexpr int RAW = Tile<float, S>::RAW, ACC = Tile<float, S>::ACC;
+    constexpr int RAW = Tile<float, S>::RAW;
     extern __shared__ unsigned char smem_raw[];
     float* F = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float* Jt = kCoef && !kPre ? F : F + 6 * T3;
-    Coef<float>* X = reinterpret_cast<Coef<float>*>(kPre ? F + 6 * T3 + ACC : F + RAW);
+    float* Jt = kCoef ? F : F + 6 * T3;
+    Coef<float>* X = reinterpret_cast<Coef<float>*>(F + RAW);
     const void* Fuse = kCoef ? static_cast<const void*>(X) : static_cast<const void*>(F);
     __shared__ uint64_t bar;
     __shared__ double red[NT / 32];
@@ -254,13 +211,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         tma_load_4d(F, &tmEB, (sc % g.nsc[0]) * S, ((sc / g.nsc[0]) % g.nsc[1]) * S, (sc / (g.nsc[0] * g.nsc[1])) * S,
                     0, &bar);
     };
-    if constexpr (kPre) {
-        // the J tile is zeroed once here, then by the merge as it reads it
-        int* const Jz = reinterpret_cast<int*>(Jt);
-        for (int i = threadIdx.x; i < ACC; i += NT) Jz[i] = 0;
-    }
     __syncthreads();
-    if (kPre && threadIdx.x == 0 && (int)blockIdx.x < nch) issue(blockIdx.x);
     const float h = pp.qdt2m_f;
     const float dtdx = pp.dtd_f[0], dtdy = CU ? dtdx : pp.dtd_f[1], dtdz = CU ? dtdx : pp.dtd_f[2];
     const float cqx = pp.cq_f[0], cqy = CU ? cqx : pp.cq_f[1], cqz = CU ? cqx : pp.cq_f[2];
@@ -272,7 +223,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
     // scale of the fixed-point tile: the largest value a move can deposit is below
     // max|cq| w_max max(dt/d) (1 + max(dt/d)^2 / 12) < 1.25 max|cq| w_max max(dt/d)
     float fxs = 1.0f;
-    double fxinv = 1.0 / (1 << (PICGB_FX64 ? FX64_LO_BITS : FX_LO_BITS));
+    double fxinv = 1.0 / (1 << FX_LO_BITS);
     {
         const float vmax = 1.25f * fmaxf(fabsf(cqx), fmaxf(fabsf(cqy), fabsf(cqz))) * fmaxf(dtdx, fmaxf(dtdy, dtdz)) *
                            *pp.wmax;
@@ -281,7 +232,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
             frexpf(vmax, &ex);  // vmax < 2^ex
             const int e = max(-120, min(120, FX_RANGE_BITS - ex));
             fxs = ldexpf(1.0f, e);
-            fxinv = ldexp(1.0, -e - (PICGB_FX64 ? FX64_LO_BITS : FX_LO_BITS));
+            fxinv = ldexp(1.0, -e - FX_LO_BITS);
         }
     }
     uint32_t phase = 0;
@@ -291,7 +242,7 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         const Chunk ch = chunks[c];
         const int scx = ch.sc % g.nsc[0], scy = (ch.sc / g.nsc[0]) % g.nsc[1], scz = ch.sc / (g.nsc[0] * g.nsc[1]);
         const int c0x = scx * S, c0y = scy * S, c0z = scz * S;
-        if (!kPre && threadIdx.x == 0) issue(c);
+        if (threadIdx.x == 0) issue(c);
         if (!kCoef)
             for (int i = threadIdx.x; i < NCP * 6 * TJ3; i += NT) Jall[i] = 0;
         const bool ok = mbar_wait_bounded(&bar, phase, WAIT_LIMIT, WAIT_LIMIT_NS);
@@ -306,13 +257,8 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         if (kCoef) {
             build_coef<float, T, NT>(F, X);
             __syncthreads();
-            if constexpr (kPre) {
-                // the raw tile is free: the next chunk's tile loads while this one runs
-                if (threadIdx.x == 0 && c + (int)gridDim.x < nch) issue(c + gridDim.x);
-            } else {
-                for (int i = threadIdx.x; i < NCP * 6 * TJ3; i += NT) Jall[i] = 0;  // the tile over the raw tile
-                __syncthreads();
-            }
+            for (int i = threadIdx.x; i < NCP * 6 * TJ3; i += NT) Jall[i] = 0;  // the tile over the raw tile
+            __syncthreads();
         }
         const int start = ch.start, end = ch.start + ch.count;
         const int ga = start / PG, gb = (end + PG - 1) / PG;
@@ -539,34 +485,17 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
         // merge: J tile cell t is domain cell c0 - 1 + t, padded index c0 + 1 + t
         for (int i = threadIdx.x; i < 3 * TJ3; i += NT) {
             int hi = 0, lo = 0;
-#if PICGB_FX64
-            long long fxv = 0;
-#pragma unroll
-            for (int cpy = 0; cpy < NCP; ++cpy) {
-                unsigned long long* Jq = reinterpret_cast<unsigned long long*>(Jall + cpy * 6 * TJ3) + i;
-                const unsigned long long q = *Jq;
-                if (kPre) *Jq = 0ull;
-                fxv += ((long long)(int)(q >> 32) << FX64_LO_BITS) + (long long)(unsigned)q;
-            }
-            hi = fxv != 0;
-#else
 #pragma unroll
             for (int cpy = 0; cpy < NCP; ++cpy) {
                 hi += Jall[cpy * 6 * TJ3 + i];
                 lo += Jall[cpy * 6 * TJ3 + 3 * TJ3 + i];
-                if (kPre) Jall[cpy * 6 * TJ3 + i] = Jall[cpy * 6 * TJ3 + 3 * TJ3 + i] = 0;
             }
-#endif
             if ((hi | lo) != 0) {
                 const int comp = i / TJ3, r = i - comp * TJ3;
                 const int tz = r / (TJ * TJ), ty = (r / TJ) % TJ, tx = r % TJ;
                 const long long o = (long long)comp * g.P + (c0x + 1 + tx) +
                                     (long long)g.np[0] * ((c0y + 1 + ty) + (long long)g.np[1] * (c0z + 1 + tz));
-#if PICGB_FX64
-                if (in_range(o, 3 * g.P)) atomicAdd(&J[o], (double)fxv * fxinv);
-#else
                 if (in_range(o, 3 * g.P)) atomicAdd(&J[o], (double)(((long long)hi << FX_LO_BITS) + lo) * fxinv);
-#endif
             }
         }
         __syncthreads();
@@ -587,8 +516,6 @@ template <int S>
 size_t push32_smem_bytes() {
     constexpr int T = S + 4;
     using TL = Tile<float, S>;
-    if (TL::kCoef && PICGB_PREFETCH)
-        return 128 + sizeof(float) * (6 * T * T * T + TL::ACC) + sizeof(Coef<float>) * 6 * TL::NE;
     if (TL::kCoef) return 128 + sizeof(float) * TL::RAW + sizeof(Coef<float>) * 6 * TL::NE;
     return 128 + sizeof(float) * (6 * T * T * T + TL::ACC);
 }

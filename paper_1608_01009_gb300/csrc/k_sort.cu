@@ -2,15 +2,16 @@
 //
 // arXiv:1608.01009 Sec. 3 stores particles per cell and Sec. 4.3 processes them
 // by supercells of S^3 cells.  On the GPU the store is one structure of arrays
-// ordered by supercell and, inside a supercell, by cell.  Every K steps
-// (K * max(dt/d) < 1, so a particle never leaves its supercell's one-cell slack
-// in between) it is re-sorted by a counting sort over cell keys
+// ordered by supercell and, inside a supercell, by cell.  Before a particle
+// could leave its supercell's one-cell slack (a fixed interval K with
+// K * max(dt/d) < 1, or the displacement bound of the host's schedule) it is
+// re-sorted by a counting sort over cell keys
 //   key = supercell * S^3 + local cell,
 // so that each supercell is a contiguous run of cell runs (the particle kernel
 // relies on the cell order: warp lanes that share a cell share their gather
 // loads and sum their currents before the shared-memory atomics):
-//   k_sort_count  : histogram of keys, warp-aggregated atomics (one atomic per
-//                   distinct key per warp); deactivated particles get no key
+//   k_sort_count  : histogram of keys, one atomic per run of equal keys in
+//                   consecutive lanes; deactivated particles get no key
 //   k_scan_tiles  : per tile of SCAN_TILE keys (whole bins), exclusive prefix
 //                   into cursor[], the tile total, its bins' tile-local starts
 //                   and the number of chunks they need
@@ -20,12 +21,13 @@
 //                   the bin starts made global and the tile's part of the
 //                   chunk table the particle kernel walks written (each bin cut
 //                   into near-equal chunks of at most CHUNK particles)
-//   k_sort_scatter_tiled: every active particle copied to its slot in the
-//                   other buffer (order inside a cell unspecified), through a
-//                   shared-memory tile written back in destination order;
-//                   deactivated particles are dropped (compaction).  It
-//                   recomputes each key from the cell it copies anyway, so no
-//                   per-particle key array is written or read.
+//   k_sort_scatter_pipe: every active particle copied to its slot in the
+//                   other buffer (order inside a cell unspecified), through
+//                   shared-memory tiles loaded one tile ahead and written back
+//                   in destination order; deactivated particles are dropped
+//                   (compaction).  It recomputes each key from the cell it
+//                   copies anyway, so no per-particle key array is written or
+//                   read.
 #include "pic_internal.cuh"
 
 namespace picgb {
@@ -42,35 +44,9 @@ __device__ __forceinline__ int cell_key(const GridDev& g, int cp) {
     return (((sc << sh) + (iz & m)) << (2 * sh)) + ((iy & m) << sh) + (ix & m);
 }
 
-// U independent warp-aggregated slot claims: every lane's U match/atomic
-// chains are issued before the first result is needed, so U atomics per lane
-// are in flight at once (one atomic per distinct key per warp and group).
-template <int U>
-__device__ __forceinline__ void warp_agg_slots(int* counters, const int (&key)[U], int (&slot)[U]) {
-    const int lane = threadIdx.x & 31;
-    unsigned peers[U];
-    int leader[U], base[U];
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-        peers[i] = __match_any_sync(0xffffffffu, key[i]);
-        leader[i] = __ffs(peers[i]) - 1;
-    }
-#pragma unroll
-    for (int i = 0; i < U; ++i)
-        base[i] = (lane == leader[i] && key[i] >= 0) ? atomicAdd(&counters[key[i]], __popc(peers[i])) : 0;
-#pragma unroll
-    for (int i = 0; i < U; ++i) {
-        const int b = __shfl_sync(0xffffffffu, base[i], leader[i]);
-        slot[i] = key[i] >= 0 ? b + __popc(peers[i] & ((1u << lane) - 1u)) : -1;
-    }
-}
-
 // Lane-interleaved groups of U x 32 particles per warp and iteration.
 constexpr int COUNT_U = 4;
 
-#ifndef PICGB_SORT_RUNS
-#define PICGB_SORT_RUNS 1
-#endif
 // Runs of equal keys in consecutive lanes (the store is sorted by key up to
 // the particles that changed cell since the last sort): `head` is the first
 // lane of this lane's run and `len` the run's length.  Equal keys in separate
@@ -100,17 +76,12 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_count(PStore<R> ps, const long
             key[i] = cp < 0 ? -1 : cell_key(g, cp);
             if (key[i] >= 0 && !in_range(key[i], (long long)g.n[0] * g.n[1] * g.n[2])) key[i] = -1;  // debug build only
         }
-#if PICGB_SORT_RUNS
 #pragma unroll
         for (int i = 0; i < COUNT_U; ++i) {
             int head, len;
             key_run(key[i], lane, head, len);
             if (lane == head && key[i] >= 0) atomicAdd(&counts[key[i]], len);
         }
-#else
-        int slot[COUNT_U];
-        warp_agg_slots<COUNT_U>(counts, key, slot);
-#endif
     }
 }
 
@@ -270,180 +241,8 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_add(int* __restrict__ counts, 
     }
 }
 
-// Tiled scatter.  A scatter that claims slots per warp (one global atomic per
-// distinct key and warp) writes every cell run in pieces claimed by different
-// warps at different times, and a piece's ends leave 32-byte sectors partly
-// written (DRAM write traffic 31% above the moved bytes, 96^3 x 32 FP32
-// capture).  Here each CTA stages a tile of TR x SORT_NT consecutive records in
-// shared memory:
-//   * keys inside a window of SW keys around the tile's first key take their
-//     rank within the tile from shared-memory counters (one claim per distinct
-//     key and warp group), the window is scanned, and each key present claims
-//     one contiguous slot range of the destination with one global atomic;
-//   * the records are placed in the tile in destination order and written out
-//     by consecutive threads to consecutive slots of each cell run;
-//   * keys outside the window (moves into far supercells) claim their slot
-//     with a global atomic and are stored directly.
-// Measured: DRAM writes equal the moved bytes (1.028 GB for 28.3 M FP32
-// particles, against +31% before); mixed 128^3 x 32 sort 0.824 -> 0.724 ms per
-// step with 4 records per thread (8: 0.776, 2: 0.822); FP64 64^3 x 50 0.163
-// -> 0.161 ms with 2 (4: 0.172).
-constexpr int SW = 1024;  // keys per window
-#ifndef PICGB_TILE_TR32
-#define PICGB_TILE_TR32 4
-#endif
-#ifndef PICGB_TILE_TR64
-#define PICGB_TILE_TR64 2
-#endif
-template <class R>
-struct TileScatter {
-    static constexpr int TR = sizeof(R) == 8 ? PICGB_TILE_TR64 : PICGB_TILE_TR32;  // records per thread
-    static constexpr int TILE = TR * SORT_NT;
-    // staged tile (cell, 3 offsets, 3 momenta, weight, id) + destination slots + window tables
-    static constexpr size_t SMEM = (size_t)TILE * (2 * sizeof(int) + 7 * sizeof(R) + sizeof(int)) + 3 * SW * sizeof(int);
-};
+constexpr int SW = 1024;  // keys per window of the scatter
 
-template <class R>
-__global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, PStore<R> dst,
-                                                               const long long* __restrict__ n_cur, GridDev g,
-                                                               int* __restrict__ cursor) {
-    constexpr int TR = TileScatter<R>::TR, TILE = TileScatter<R>::TILE;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* s_off = reinterpret_cast<R*>(smem_raw);                 // 3 x TILE
-    R* s_u = s_off + 3 * TILE;                                   // 3 x TILE
-    R* s_w = s_u + 3 * TILE;                                     // TILE
-    int* s_cell = reinterpret_cast<int*>(s_w + TILE);           // TILE
-    int* s_id = s_cell + TILE;                                   // TILE
-    int* s_slot = s_id + TILE;                                   // TILE
-    int* s_cnt = s_slot + TILE;                                  // SW: counts, then tile positions
-    int* s_gb = s_cnt + SW;                                      // SW: global slot of each key's range
-    int* s_scan = s_gb + SW;                                     // SW / 4 scan scratch (first 32 used)
-    __shared__ int s_kb, s_nw;
-    const long long N = *n_cur;
-    const int lane = threadIdx.x & 31;
-    const long long ntile = (N + TILE - 1) / TILE;
-    for (long long t = blockIdx.x; t < ntile; t += gridDim.x) {
-        const long long base = t * TILE;
-        // window: from a quarter window below the first active key of the tile's first 32 records
-        if (threadIdx.x < 32) {
-            const long long p = base + lane;
-            const int cp = p < N ? src.cell[p] : INACTIVE;
-            const unsigned act = __ballot_sync(0xffffffffu, cp >= 0);
-            const int k = cp >= 0 ? cell_key(g, cp) : 0;
-            const int k0 = __shfl_sync(0xffffffffu, k, act ? __ffs(act) - 1 : 0);
-            if (lane == 0) s_kb = act ? max(0, k0 - SW / 4) : 0;
-        }
-        for (int i = threadIdx.x; i < SW; i += SORT_NT) s_cnt[i] = 0;
-        if (threadIdx.x < 32) s_scan[threadIdx.x] = 0;  // the block scan reads 32 warp totals; 8 warps write theirs
-        __syncthreads();
-        const int kb = s_kb;
-        int key[TR], rank[TR], cell[TR], id[TR];
-        R off[TR][3], u[TR][3], w[TR];
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            const long long p = base + (long long)i * SORT_NT + threadIdx.x;
-            key[i] = -1;
-            if (p < N) {
-                cell[i] = src.cell[p];
-                key[i] = cell[i] < 0 ? -1 : cell_key(g, cell[i]);
-                if (key[i] >= 0 && !in_range(key[i], (long long)g.n[0] * g.n[1] * g.n[2])) key[i] = -1;  // debug only
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    off[i][a] = src.off[a][p];
-                    u[i][a] = src.u[a][p];
-                }
-                w[i] = src.w[p];
-                id[i] = src.id[p];
-            }
-        }
-        // ranks: in-window keys from the shared counters, the others from the global cursor
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            const bool inw = key[i] >= kb && key[i] < kb + SW;
-            // lanes outside the window or without a record form groups of their own
-            const unsigned peers = __match_any_sync(0xffffffffu, inw ? key[i] : -2 - lane);
-            const int leader = __ffs(peers) - 1;
-            int b = 0;
-            if (lane == leader) {
-                if (inw) b = atomicAdd(&s_cnt[key[i] - kb], __popc(peers));
-                else if (key[i] >= 0) b = atomicAdd(&cursor[key[i]], 1);
-            }
-            b = __shfl_sync(0xffffffffu, b, leader);
-            rank[i] = key[i] >= 0 ? b + __popc(peers & ((1u << lane) - 1u)) : -1;
-        }
-        __syncthreads();
-        // exclusive scan of the window counts (tile positions); one global claim per key present
-        {
-            constexpr int PER = SW / SORT_NT;
-            int c[PER], sum = 0;
-#pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                c[j] = s_cnt[threadIdx.x * PER + j];
-                sum += c[j];
-            }
-            int total;
-            int run = block_exclusive_scan(sum, s_scan, &total);
-#pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                const int k = threadIdx.x * PER + j;
-                s_cnt[k] = run;
-                s_gb[k] = c[j] && in_range(kb + k, (long long)g.n[0] * g.n[1] * g.n[2]) ? atomicAdd(&cursor[kb + k], c[j])
-                                                                                       : 0;
-                run += c[j];
-            }
-            if (threadIdx.x == 0) s_nw = total;
-        }
-        __syncthreads();
-        // place the in-window records in destination order; store the others directly
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            if (key[i] < 0) continue;
-            if (key[i] >= kb && key[i] < kb + SW) {
-                const int tp = s_cnt[key[i] - kb] + rank[i];
-                if (!in_range(tp, TILE)) continue;  // debug build only
-                s_slot[tp] = s_gb[key[i] - kb] + rank[i];
-                s_cell[tp] = cell[i];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    s_off[a * TILE + tp] = off[i][a];
-                    s_u[a * TILE + tp] = u[i][a];
-                }
-                s_w[tp] = w[i];
-                s_id[tp] = id[i];
-            } else {
-                const int q = rank[i];
-                if (!in_range(q, N)) continue;  // debug build only
-                dst.cell[q] = cell[i];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    dst.off[a][q] = off[i][a];
-                    dst.u[a][q] = u[i][a];
-                }
-                dst.w[q] = w[i];
-                dst.id[q] = id[i];
-            }
-        }
-        __syncthreads();
-        const int nw = s_nw;
-        for (int tp = threadIdx.x; tp < nw; tp += SORT_NT) {
-            const int q = s_slot[tp];
-            if (!in_range(q, N)) continue;  // debug build only
-            dst.cell[q] = s_cell[tp];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                dst.off[a][q] = s_off[a * TILE + tp];
-                dst.u[a][q] = s_u[a * TILE + tp];
-            }
-            dst.w[q] = s_w[tp];
-            dst.id[q] = s_id[tp];
-        }
-        __syncthreads();
-    }
-}
-
-#ifndef PICGB_SORT_PIPE
-#define PICGB_SORT_PIPE 1
-#endif
 #ifndef PICGB_PIPE_TILE32
 #define PICGB_PIPE_TILE32 1024
 #endif
@@ -454,14 +253,24 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_scatter_tiled(PStore<R> src, P
 #define PICGB_PIPE_NT 256
 #endif
 constexpr int PIPE_NT = PICGB_PIPE_NT;  // threads of the pipelined scatter
-// Pipelined tiled scatter: the same ranking, window scan and one claim per key
-// and tile as k_sort_scatter_tiled, but the tile's records are not held in
-// registers.  Each CTA keeps two tile stages in shared memory, filled by bulk
-// asynchronous copies (one per array) that run while the previous tile is
-// ranked and written: tile t+gridDim loads during tile t.  Records stay in
-// their stage; the window's records are written out through a permutation
-// (s_src: stage position of each destination-ordered slot), so consecutive
-// threads still write consecutive slots of each cell run.
+// Pipelined tiled scatter.  A scatter that claims slots per warp writes every
+// cell run in pieces claimed by different warps at different times, and a
+// piece's ends leave 32-byte sectors partly written (DRAM writes 31% above the
+// moved bytes on a 96^3 x 32 FP32 capture).  Here each CTA takes tiles of
+// consecutive records:
+//   * keys inside a window of SW keys from a quarter window below the tile's
+//     first key take their rank within the tile from shared-memory counters
+//     (one claim per run of equal keys), the window is scanned, and each key
+//     present claims one contiguous slot range of the destination with one
+//     global atomic;
+//   * keys outside the window (moves into far supercells) claim their slots
+//     from the global cursor and are stored directly;
+//   * the window's records are written out through a permutation (s_src: the
+//     stage position of each destination-ordered slot), so consecutive threads
+//     write consecutive slots of each cell run.
+// The records are not held in registers: each CTA keeps two tile stages in
+// shared memory, filled by bulk asynchronous copies (one per array) while the
+// previous tile is ranked and written (tile t + gridDim loads during tile t).
 template <class R>
 struct PipeScatter {
     static constexpr int TILE = sizeof(R) == 8 ? PICGB_PIPE_TILE64 : PICGB_PIPE_TILE32;  // records per tile
@@ -562,7 +371,6 @@ __global__ void __launch_bounds__(PIPE_NT) k_sort_scatter_pipe(PStore<R> src, PS
                 if (key[i] >= 0 && !in_range(key[i], nkeys)) key[i] = -1;  // debug build only
             }
             const bool inw = key[i] >= kb && key[i] < kb + SW;
-#if PICGB_SORT_RUNS
             // a run of one key claims its ranks with one atomic: in-window keys from
             // the shared counters, the others from the global cursor
             int head, len;
@@ -574,18 +382,6 @@ __global__ void __launch_bounds__(PIPE_NT) k_sort_scatter_pipe(PStore<R> src, PS
             }
             b = __shfl_sync(0xffffffffu, b, head);
             rank[i] = key[i] >= 0 ? b + lane - head : -1;
-#else
-            // lanes outside the window or without a record form groups of their own
-            const unsigned peers = __match_any_sync(0xffffffffu, inw ? key[i] : -2 - lane);
-            const int leader = __ffs(peers) - 1;
-            int b = 0;
-            if (lane == leader) {
-                if (inw) b = atomicAdd(&s_cnt[key[i] - kb], __popc(peers));
-                else if (key[i] >= 0) b = atomicAdd(&cursor[key[i]], 1);
-            }
-            b = __shfl_sync(0xffffffffu, b, leader);
-            rank[i] = key[i] >= 0 ? b + __popc(peers & ((1u << lane) - 1u)) : -1;
-#endif
         }
         __syncthreads();
         // exclusive scan of the window counts (tile positions); one global claim per key present
@@ -671,25 +467,12 @@ cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> sr
     k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, tile_nch, ntiles, g.nbins, bin_start, n_next, nchunks);
     k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, tile_nch, ntiles, n_next, kpb, bin_start,
                                            chunks);
-#if PICGB_SORT_PIPE
-    {
-        constexpr int sm = (int)PipeScatter<R>::SMEM;
-        const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_pipe<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e != cudaSuccess) return e;
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter_pipe<R>, PIPE_NT, sm);
-        k_sort_scatter_pipe<R><<<nsm * (per_sm > 0 ? per_sm : 1), PIPE_NT, sm, st>>>(src, dst, n_cur, g, cursor, err);
-        return cudaGetLastError();
-    }
-#endif
-    (void)err;
-    const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)TileScatter<R>::SMEM);
+    constexpr int sm = (int)PipeScatter<R>::SMEM;
+    const cudaError_t e = cudaFuncSetAttribute(k_sort_scatter_pipe<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter_tiled<R>, SORT_NT, TileScatter<R>::SMEM);
-    k_sort_scatter_tiled<R><<<nsm * (per_sm > 0 ? per_sm : 1), SORT_NT, TileScatter<R>::SMEM, st>>>(src, dst, n_cur,
-                                                                                                   g, cursor);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter_pipe<R>, PIPE_NT, sm);
+    k_sort_scatter_pipe<R><<<nsm * (per_sm > 0 ? per_sm : 1), PIPE_NT, sm, st>>>(src, dst, n_cur, g, cursor, err);
     return cudaGetLastError();
 }
 
