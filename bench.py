@@ -487,6 +487,12 @@ def run_profile_case(args):
         return 0
     if args.profile_case in ("fp64", "tsc"):
         wl, prec = W.config("c2"), "fp64"
+    elif args.profile_case == "fields":
+        # the laser ramp's grid (256 x 128 x 128, x absorbing: the field arrays, 0.4 GB, exceed L2)
+        # with one electron per cell, for the field kernels
+        wl = W.uniform_plasma((256, 128, 128), 1, 0.05, 0.1, seed=1242, steps=args.steps, name="fields-256")
+        wl.bc = (1, 0, 0)
+        prec = "mixed"
     else:
         wl, prec = W.uniform_plasma((96, 96, 96), 32, 0.05, 0.1, seed=1241, steps=args.steps, name="mixed-96"), "mixed"
     r = time_gpu(torch, pic, wl, prec, args.steps, args.warmup, form_factor=ff)
@@ -660,7 +666,7 @@ def main():
     ap.add_argument("--no-laser-ramp", action="store_true", help="skip the c5 laser-plasma run and its adjoint")
     ap.add_argument("--laser-ramp", action="store_true",
                     help="run only the 134 M-particle laser-plasma workload with its 50-step adjoint")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed", "tsc", "adjoint"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "tsc", "adjoint", "fields"], default=None,
                     help="run only one reduced case for ncu captures (a few GB on the device): "
                          "fp64 = the 64^3 x 50 FP64 plasma, mixed = a 96^3 x 32 mixed plasma, "
                          "tsc = the 64^3 x 50 plasma with the second-order form factor, "

@@ -558,6 +558,10 @@ __device__ __forceinline__ double damp_of(const GridDev& g, int comp, bool magne
     const int ijk[3] = {i, j, k};
     for (int a = 0; a < 3; ++a) {
         if (g.bc[a] == 0 || g.absorb_cells <= 0) continue;
+        if (g.damp) {  // the forward's table of the same factors
+            f *= g.damp[g.damp_off[a] + (stag(comp, a, magnetic) != 0.0 ? g.n[a] : 0) + ijk[a]];
+            continue;
+        }
         const double pos = ijk[a] + stag(comp, a, magnetic);
         const double dist = fmin(pos, (double)g.n[a] - pos);
         const double L = (double)g.absorb_cells;

@@ -17,6 +17,7 @@ namespace picgb {
 cudaError_t fdtd_b_launch(cudaStream_t, double*, const GridDev&, double, int, float*, double*);
 cudaError_t fdtd_e_launch(cudaStream_t, double*, double*, double*, const GridDev&);
 cudaError_t refresh_launch(cudaStream_t, double*, const GridDev&, float*);
+cudaError_t damp_table_launch(cudaStream_t, const GridDev&, double*);
 cudaError_t field_energy_launch(cudaStream_t, const double*, const GridDev&, double*);
 int fdtd_blocks(const GridDev&);
 template <class R>
@@ -1136,6 +1137,10 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
     g.absorb_cells = gd->absorb_cells;
     g.absorb_sigma = gd->absorb_sigma;
     g.absorb_rL = gd->absorb_cells > 0 ? 1.0 / gd->absorb_cells : 0.0;
+    g.damp = nullptr;
+    g.damp_off[0] = 0;
+    g.damp_off[1] = 2 * g.n[0];
+    g.damp_off[2] = 2 * (g.n[0] + g.n[1]);
     // the default interval (sort_interval 0), measured on the 64^3 x 50 FP64, 128^3 x 32 mixed and
     // laser-ramp workloads: the FP64 cloud-in-cell kernel runs 13% faster on particles sorted
     // every step, which outweighs the sorts; the second-order kernel (one thread per particle,
@@ -1171,6 +1176,15 @@ int pic_create(const pic_grid_desc* gd, pic_ctx** out) {
     if ((r = dalloc(c, c->allocs, &c->d_counter, 1))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_wf, fdtd_blocks(g)))) return bail(r);
     if ((r = dalloc(c, c->allocs, &c->d_energy, 2))) return bail(r);
+    if ((g.bc[0] | g.bc[1] | g.bc[2]) != 0 && g.absorb_cells > 0) {
+        double* tab = nullptr;
+        if ((r = dalloc(c, c->allocs, &tab, 2 * (g.n[0] + g.n[1] + g.n[2])))) return bail(r);
+        if ((e = damp_table_launch(c->st, g, tab)) != cudaSuccess) {
+            fail(c, PIC_ERR_CUDA, "init: %s", cudaGetErrorString(e));
+            return bail(PIC_ERR_CUDA);
+        }
+        g.damp = tab;  // every later copy of g (kernel arguments) reads the table
+    }
     if (c->adaptive) {
         if ((r = dalloc(c, c->allocs, &c->d_drift, DRIFT_ROWS))) return bail(r);
         cudaMemsetAsync(c->d_drift, 0, DRIFT_ROWS * sizeof(unsigned), c->st);

@@ -89,6 +89,11 @@ struct GridDev {
     int absorb_cells;
     double absorb_sigma;
     double absorb_rL;  // 1 / absorb_cells (0 without a layer)
+    // absorbing layer factors per axis, lattice index and staggering (device,
+    // 2 n[a] doubles from damp_off[a]: whole then half-shifted points); null:
+    // formed in the field kernels from the formula
+    const double* damp;
+    int damp_off[3];
 };
 
 template <class R>
