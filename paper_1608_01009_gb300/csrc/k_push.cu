@@ -270,14 +270,18 @@ __device__ void split_direct(R* Jt, int k0, R ax, R ay, R az, R dx, R dy, R dz, 
 // particle pass valid = false).  Returns w (gamma - 1) of the new state.
 // CU: cubic cells, so dt/d and the current factor q/(dt d d) are the same on
 // every axis (one multiply each instead of three).
-template <class R, int S, int NT, bool CU>
-__device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const PStore<R>& ps, int p, bool valid,
-                                       const PushParams& pp, int c0x, int c0y, int c0z, int* err,
-                                       const XQueue<R>& xq, int qbase, int* s_qn) {
+// G: the particle in slot p of the sorted order is particle perm[p] of `pin`
+// (the sort computed ranks only); its whole record goes to slot p of `ps`.
+// Otherwise pin is ps and the particle is updated in place.
+template <class R, int S, int NT, bool CU, bool G>
+__device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const PStore<R>& ps, const PStore<R>& pin,
+                                       const int* __restrict__ perm, int p, bool valid, const PushParams& pp, int c0x,
+                                       int c0y, int c0z, int* err, const XQueue<R>& xq, int qbase, int* s_qn) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3;
     constexpr bool kMom = Tile<R, S>::kMoments;
     const GridDev& g = pp.g;
-    const int cp = valid ? ps.cell[p] : INACTIVE;
+    const int q = G && valid ? perm[p] : p;  // where the particle is read
+    const int cp = valid ? pin.cell[q] : INACTIVE;
     bool act = cp >= 0;  // negative: no particle, or deactivated at an absorbing boundary
     int gx = cell_x(cp), gy = cell_y(cp), gz = cell_z(cp);
     // cell relative to the supercell origin: the periodic image next to the tile
@@ -293,13 +297,27 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
     if (!act) lx = ly = lz = 0;
     R fx = R(0.25), fy = R(0.25), fz = R(0.25), ux = R(0), uy = R(0), uz = R(0), w = R(0);
     if (act) {
-        fx = ps.off[0][p];
-        fy = ps.off[1][p];
-        fz = ps.off[2][p];
-        ux = ps.u[0][p];
-        uy = ps.u[1][p];
-        uz = ps.u[2][p];
-        w = ps.w[p];
+        fx = pin.off[0][q];
+        fy = pin.off[1][q];
+        fz = pin.off[2][q];
+        ux = pin.u[0][q];
+        uy = pin.u[1][q];
+        uz = pin.u[2][q];
+        w = pin.w[q];
+    }
+    if (G && valid) {
+        // the record's constant fields move with it; a particle dropped below
+        // keeps its (unused) offsets and momenta
+        ps.w[p] = pin.w[q];
+        ps.id[p] = pin.id[q];
+        if (!act) {
+            ps.cell[p] = cp;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                ps.off[a][p] = pin.off[a][q];
+                ps.u[a][p] = pin.u[a][q];
+            }
+        }
     }
 
     // ---- gather: each component from its own staggered lattice (tile origin = cell c0-2)
@@ -359,6 +377,13 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
         // cannot happen while K * max(dt/d) < 1; record it, drop the particle, touch no tile
         atomicOr(err, ERRBIT_DRIFT);
         ps.cell[p] = INACTIVE | cp;
+        if (G) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                ps.off[a][p] = pin.off[a][q];
+                ps.u[a][p] = pin.u[a][q];
+            }
+        }
         act = false;
     }
 
@@ -431,9 +456,10 @@ __device__ __forceinline__ R push_lane(const void* __restrict__ Fv, R* Jt, const
 
 // Two resident CTAs of 256 threads per SM (the kernel needs about 100
 // registers; its shared tile is 106 KB at S = 4).
-template <class R, int S, int NT, bool CU>
+template <class R, int S, int NT, bool CU, bool G>
 __global__ void __launch_bounds__(NT, 2) k_push(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<R> ps,
-                                            XQueue<R> xq, const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
+                                            PStore<R> pin, const int* __restrict__ perm, XQueue<R> xq,
+                                            const Chunk* __restrict__ chunks, const int* __restrict__ nchunks,
                                             double* __restrict__ J, double* __restrict__ ek_part,
                                             int* __restrict__ err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
@@ -492,7 +518,8 @@ __global__ void __launch_bounds__(NT, 2) k_push(const __grid_constant__ CUtensor
         R ek_chunk = R(0);  // at most CHUNK / NT particles per lane
         for (int base = ch.start + warp * 32; base < end; base += NT) {
             const int p = base + lane;
-            ek_chunk += push_lane<R, S, NT, CU>(Fuse, Jt, ps, p, p < end, pp, c0x, c0y, c0z, err, xq, qbase, &s_qn);
+            ek_chunk += push_lane<R, S, NT, CU, G>(Fuse, Jt, ps, pin, perm, p, p < end, pp, c0x, c0y, c0z, err, xq,
+                                                   qbase, &s_qn);
         }
         ek += (double)ek_chunk;
         __syncthreads();
@@ -554,32 +581,44 @@ size_t push_smem_bytes() {
 template <class R, int S>
 cudaError_t push_setup(int* blocks_per_sm) {
     const int sm = (int)push_smem_bytes<R, S>();
-    cudaError_t e = cudaFuncSetAttribute(k_push<R, S, PUSH_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_push<R, S, PUSH_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = cudaSuccess;
+    for (auto f : {k_push<R, S, PUSH_NT, true, false>, k_push<R, S, PUSH_NT, false, false>,
+                   k_push<R, S, PUSH_NT, true, true>, k_push<R, S, PUSH_NT, false, true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R, S, PUSH_NT, false>, PUSH_NT, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R, S, PUSH_NT, false, false>, PUSH_NT,
+                                                         sm);
 }
 
+// perm null: the particles are updated in place in ps.  Otherwise slot i of
+// ps receives particle perm[i] of pin, updated (pin and ps are the store's
+// two buffers; the sort computed ranks only).
 template <class R, int S>
 cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
-                        const XQueue<R>& xq, const Chunk* chunks, const int* nchunks, double* J, double* ek_part,
-                        int* err) {
+                        const PStore<R>& pin, const int* perm, const XQueue<R>& xq, const Chunk* chunks,
+                        const int* nchunks, double* J, double* ek_part, int* err) {
     const bool cubic = pp.g.d[0] == pp.g.d[1] && pp.g.d[1] == pp.g.d[2];
-    if (cubic)
-        k_push<R, S, PUSH_NT, true><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, xq, chunks, nchunks, J,
-                                                                               ek_part, err);
+    const size_t sm = push_smem_bytes<R, S>();
+    if (cubic && perm)
+        k_push<R, S, PUSH_NT, true, true><<<grid, PUSH_NT, sm, st>>>(tm, pp, ps, pin, perm, xq, chunks, nchunks, J,
+                                                                    ek_part, err);
+    else if (cubic)
+        k_push<R, S, PUSH_NT, true, false><<<grid, PUSH_NT, sm, st>>>(tm, pp, ps, ps, nullptr, xq, chunks, nchunks, J,
+                                                                     ek_part, err);
+    else if (perm)
+        k_push<R, S, PUSH_NT, false, true><<<grid, PUSH_NT, sm, st>>>(tm, pp, ps, pin, perm, xq, chunks, nchunks, J,
+                                                                     ek_part, err);
     else
-        k_push<R, S, PUSH_NT, false><<<grid, PUSH_NT, push_smem_bytes<R, S>(), st>>>(tm, pp, ps, xq, chunks, nchunks,
-                                                                                J, ek_part, err);
+        k_push<R, S, PUSH_NT, false, false><<<grid, PUSH_NT, sm, st>>>(tm, pp, ps, ps, nullptr, xq, chunks, nchunks,
+                                                                      J, ek_part, err);
     return cudaGetLastError();
 }
 
 #define PICGB_PUSH_INST(R, S)                                                                                   \
     template cudaError_t push_setup<R, S>(int*);                                                                \
     template cudaError_t push_launch<R, S>(int, cudaStream_t, const CUtensorMap&, const PushParams&,            \
-                                           const PStore<R>&, const XQueue<R>&, const Chunk*, const int*, double*, \
-                                           double*, int*);
+                                           const PStore<R>&, const PStore<R>&, const int*, const XQueue<R>&,    \
+                                           const Chunk*, const int*, double*, double*, int*);
 PICGB_PUSH_INST(double, 2)
 PICGB_PUSH_INST(double, 4)
 PICGB_PUSH_INST(double, 8)

@@ -447,6 +447,34 @@ __global__ void __launch_bounds__(PIPE_NT) k_sort_scatter_pipe(PStore<R> src, PS
     }
 }
 
+// Ranks only: each active particle's destination slot, as perm[slot] = its
+// index in the current store (one atomic per run of equal keys in consecutive
+// lanes).  The FP64 particle kernel then reads particle perm[i] and writes it
+// to slot i of the other buffer, so the particles move once per step instead
+// of twice (scatter, then push in place).
+template <class R>
+__global__ void __launch_bounds__(SORT_NT) k_sort_rank(PStore<R> ps, const long long* __restrict__ n_cur,
+                                                      const long long* __restrict__ n_next, GridDev g,
+                                                      int* __restrict__ cursor, int* __restrict__ perm) {
+    const long long N = *n_cur, M = *n_next;
+    const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * SORT_NT;
+    for (long long b = (long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31); b < N; b += stride) {
+        const long long p = b + lane;
+        const int cp = p < N ? ps.cell[p] : INACTIVE;
+        int key = cp < 0 ? -1 : cell_key(g, cp);
+        if (key >= 0 && !in_range(key, nkeys)) key = -1;  // debug build only
+        int head, len;
+        key_run(key, lane, head, len);
+        int s0 = 0;
+        if (lane == head && key >= 0) s0 = atomicAdd(&cursor[key], len);
+        s0 = __shfl_sync(0xffffffffu, s0, head);
+        const long long slot = (long long)s0 + (lane - head);
+        if (key >= 0 && in_range(slot, M)) perm[slot] = (int)p;
+    }
+}
+
 int sort_grid(int nsm) { return nsm * 8; }
 
 long long sort_tiles(long long nkeys) { return (nkeys + SCAN_TILE - 1) / SCAN_TILE; }
@@ -475,6 +503,28 @@ cudaError_t sort_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> sr
     k_sort_scatter_pipe<R><<<nsm * (per_sm > 0 ? per_sm : 1), PIPE_NT, sm, st>>>(src, dst, n_cur, g, cursor, err);
     return cudaGetLastError();
 }
+
+// The sort without its data movement: count, scans, chunk table, and the
+// destination permutation of the current store (see k_sort_rank).
+template <class R>
+cudaError_t sort_rank_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<R> src, const long long* n_cur,
+                             long long* n_next, int* counts, int* cursor, int* tile_sum, int* bin_start,
+                             Chunk* chunks, int* nchunks, int* perm) {
+    const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int ntiles = (int)sort_tiles(nkeys);
+    const int kpb = g.S * g.S * g.S;
+    int* tile_nch = tile_sum + ntiles;
+    k_sort_count<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, n_cur, g, counts);
+    k_scan_tiles<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, kpb, bin_start, tile_nch);
+    k_scan_top<<<1, SCAN_NT, 0, st>>>(tile_sum, tile_nch, ntiles, g.nbins, bin_start, n_next, nchunks);
+    k_scan_add<<<ntiles, SCAN_NT, 0, st>>>(counts, nkeys, cursor, tile_sum, tile_nch, ntiles, n_next, kpb, bin_start,
+                                           chunks);
+    k_sort_rank<R><<<sort_grid(nsm), SORT_NT, 0, st>>>(src, n_cur, n_next, g, cursor, perm);
+    return cudaGetLastError();
+}
+
+template cudaError_t sort_rank_launch<double>(cudaStream_t, int, const GridDev&, PStore<double>, const long long*,
+                                              long long*, int*, int*, int*, int*, Chunk*, int*, int*);
 
 template cudaError_t sort_launch<double>(cudaStream_t, int, const GridDev&, PStore<double>, PStore<double>,
                                          const long long*, long long*, int*, int*, int*, int*, Chunk*, int*, int*);

@@ -23,6 +23,9 @@ int fdtd_blocks(const GridDev&);
 template <class R>
 cudaError_t sort_launch(cudaStream_t, int, const GridDev&, PStore<R>, PStore<R>, const long long*, long long*, int*,
                         int*, int*, int*, Chunk*, int*, int*);
+template <class R>
+cudaError_t sort_rank_launch(cudaStream_t, int, const GridDev&, PStore<R>, const long long*, long long*, int*, int*,
+                             int*, int*, Chunk*, int*, int*);
 long long sort_tiles(long long nkeys);
 long long sort_tile_scratch(long long nkeys);
 template <class R>
@@ -71,6 +74,10 @@ struct Store {
 
 struct Species {
     double q = 0, m = 1;
+    // FP64: destination permutation of the last ranks-only sort (cap ints); the
+    // next particle kernel moves the store through it into the other buffer
+    int* d_perm = nullptr;
+    bool perm_pending = false;
     bool immobile = false;         // neutralising background: no particles stored
     long long cap = 0;
     Store<double> s64;
@@ -341,8 +348,28 @@ int sort_species(pic_ctx* c, Species& s) {
     return PIC_OK;
 }
 
+// The sort before a step of the FP64 cloud-in-cell path: ranks only (count,
+// scans, chunk table, destination permutation); the particle kernel that
+// follows moves the particles through the permutation into the other buffer.
+int sort_all_ranks(pic_ctx* c) {
+    for (auto& s : c->sp) {
+        if (s.immobile) continue;
+        Store<double>& st = s.s64;
+        cudaError_t e = sort_rank_launch<double>(c->st, c->nsm, c->g, st.a(), s.d_n, s.d_n + 1, c->d_counts,
+                                                 c->d_cursor, c->d_tile_sum, s.d_bin_start, s.d_chunks, s.d_nchunks,
+                                                 s.d_perm);
+        if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "sort launch: %s", cudaGetErrorString(e));
+        c->launches += 5;
+        s.perm_pending = true;
+        CUDA_TRY(c, cudaMemcpyAsync(s.d_n, s.d_n + 1, sizeof(long long), cudaMemcpyDeviceToDevice, c->st));
+    }
+    c->since_sort = 0;
+    return PIC_OK;
+}
+
 int sort_all(pic_ctx* c) {
     for (auto& s : c->sp) {
+        s.perm_pending = false;  // a full sort rebuilds the order from the current buffer
         if (s.immobile) continue;  // empty store, never pushed
         int r = c->mixed ? sort_species<float>(c, s) : sort_species<double>(c, s);
         if (r) return r;
@@ -423,15 +450,23 @@ int push_species(pic_ctx* c, Species& s) {
     PStore<R>& ps = store_of<R>(s).a();
     const int S = c->g.S;
     if constexpr (sizeof(R) == 8) {
+        // after a ranks-only sort: read the current buffer through the permutation, write the other
+        const bool g = s.perm_pending;
+        PStore<R>& out = g ? store_of<R>(s).b() : ps;
+        const int* perm = g ? s.d_perm : nullptr;
         if (S == 2)
-            e = push_launch<double, 2>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
-                                       c->d_err);
+            e = push_launch<double, 2>(c->push_grid, c->st, tm, pp, out, ps, perm, xq, s.d_chunks, s.d_nchunks, c->J,
+                                       s.d_ek, c->d_err);
         if (S == 4)
-            e = push_launch<double, 4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
-                                       c->d_err);
+            e = push_launch<double, 4>(c->push_grid, c->st, tm, pp, out, ps, perm, xq, s.d_chunks, s.d_nchunks, c->J,
+                                       s.d_ek, c->d_err);
         if (S == 8)
-            e = push_launch<double, 8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
-                                       c->d_err);
+            e = push_launch<double, 8>(c->push_grid, c->st, tm, pp, out, ps, perm, xq, s.d_chunks, s.d_nchunks, c->J,
+                                       s.d_ek, c->d_err);
+        if (g && e == cudaSuccess) {
+            store_of<R>(s).cur ^= 1;
+            s.perm_pending = false;
+        }
     } else {
         if (c->adaptive) pp.drift = c->d_drift + std::min(c->since_sort, DRIFT_ROWS - 1);
         if (S == 4)
@@ -468,6 +503,11 @@ int alloc_store(pic_ctx* c, Species& s, Store<R>& st, long long cap) {
         if (!r) r = dalloc(c, s.allocs, &p.id, cap);
         if (r) return r;
     }
+    if (sizeof(R) == 8) {
+        int r = dalloc(c, s.allocs, &s.d_perm, cap);
+        if (r) return r;
+    }
+    s.perm_pending = false;
     st.cur = 0;
     return PIC_OK;
 }
@@ -485,6 +525,8 @@ void free_species(Species& s) {
     s.d_nchunks = nullptr;
     s.d_stage = nullptr;
     s.d_wmax = nullptr;
+    s.d_perm = nullptr;
+    s.perm_pending = false;
 }
 
 // Device address of a page-locked host array (cudaHostAlloc / cudaHostRegister,
@@ -1412,7 +1454,9 @@ int pic_step(pic_ctx* c, int nsteps) {
         if (rd) return rd;
         if (due) {
             stage_begin(c, 2, &e0);
-            int r = sort_all(c);
+            // FP64 cloud-in-cell: the particle kernel below moves the particles
+            const bool ranks = !c->mixed && c->desc.form_factor != 2;
+            int r = ranks ? sort_all_ranks(c) : sort_all(c);
             if (r) return r;
             stage_end(c, 2, e0);
         }

@@ -324,8 +324,8 @@ template <class R, int S>
 cudaError_t push_setup(int* blocks_per_sm);
 template <class R, int S>
 cudaError_t push_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp, const PStore<R>& ps,
-                        const XQueue<R>& xq, const Chunk* chunks, const int* nchunks, double* J, double* ek_part,
-                        int* err);
+                        const PStore<R>& pin, const int* perm, const XQueue<R>& xq, const Chunk* chunks,
+                        const int* nchunks, double* J, double* ek_part, int* err);
 // mixed-precision particle kernel (k_push32.cu, S = 4, 8)
 template <int S>
 cudaError_t push32_setup(int* blocks_per_sm);
