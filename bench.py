@@ -53,7 +53,12 @@ FLOPS_PER_PARTICLE_TSC = 1031
 # Minimum HBM traffic per particle-step of the particle store:
 #   FP64 store: read cell(4) + offset(24) + u(24) + w(8) = 60 B, write cell + offset + u = 52 B.
 #   mixed store: read 4 + 12 + 12 + 4 = 32 B, write 4 + 12 + 12 = 28 B.
-BYTES_PER_PARTICLE = {"fp64": 112, "mixed": 60}
+# The launch right after a sort also moves the records to the other buffer
+# through the sort's permutation (the sort computes ranks only): mixed store
+# read cell + offset + u + w + id + perm index = 40 B, write the whole record
+# (cell, offset, u, w, id) = 36 B; FP64 store read 4 + 24 + 24 + 8 + 4 + 4 = 68 B,
+# write 64 B.
+BYTES_PER_PARTICLE = {"fp64": 112, "fp64_after_sort": 132, "mixed": 60, "mixed_after_sort": 76}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (context; the roofline divides by the in-run probe)
 
 
@@ -526,7 +531,9 @@ def run_gpu(args):
     value = weak_value(r["npart"], ws, args.steps, ms)
     push_ms = r["stage_ms"]["push_deposit"]
     flops = FLOPS_PER_PARTICLE * r["npart"]
-    bytes_ = BYTES_PER_PARTICLE["fp64"] * r["npart"]
+    nsorts = max(0, (r["launches"] - 5 * args.steps) // 5)  # each followed by a launch that moves the records
+    bytes_ = (BYTES_PER_PARTICLE["fp64"] * (args.steps - nsorts) + BYTES_PER_PARTICLE["fp64_after_sort"] * nsorts) \
+        / args.steps * r["npart"]
     achieved_tf = flops / (push_ms / 1e3) / 1e12
     achieved_gbs = bytes_ / (push_ms / 1e3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -563,7 +570,11 @@ def run_gpu(args):
             r3 = time_gpu(torch, pic, wl3, "mixed", args.steps, args.warmup)
         ms3 = _barrier_max(torch, r3["ms"], ws)
         pm = r3["stage_ms"]["push_deposit"]
-        gbs = BYTES_PER_PARTICLE["mixed"] * r3["npart"] / (pm / 1e3) / 1e9
+        # launches right after a sort (the 5 sort kernels per sort come on top of 5 per step)
+        nsorts = max(0, (r3["launches"] - 5 * args.steps) // 5)
+        per_launch_b = (BYTES_PER_PARTICLE["mixed"] * (args.steps - nsorts) +
+                        BYTES_PER_PARTICLE["mixed_after_sort"] * nsorts) / args.steps
+        gbs = per_launch_b * r3["npart"] / (pm / 1e3) / 1e9
         out["mixed"] = {"value": r3["npart"] * ws * args.steps / (ms3 / 1e3), "unit": UNIT, "dtype": "f32/f64",
                         "config": {"workload": _workload_desc(wl3, "mixed FP32/FP64"),
                                    "sort_schedule": "displacement-bounded (the mixed default, sort_interval 0)"},
@@ -571,7 +582,8 @@ def run_gpu(args):
                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                      "frac": gbs / hbm_peak, "traffic": _traffic("mixed"),
                                      "kernel": "k_push_g<4> (mixed gather + Boris + move + VB deposit)",
-                                     "per_launch_ms": pm},
+                                     "per_launch_ms": pm, "bytes_per_particle": per_launch_b,
+                                     "launches_after_sort": nsorts, "launches": args.steps},
                         "stage_ms_per_step": {k: round(v, 4) for k, v in r3["stage_ms"].items()},
                         "gpu_launches": r3["launches"], "clocks": clk3.summary()}
         r3["sim"].close()

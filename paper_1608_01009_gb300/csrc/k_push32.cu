@@ -178,9 +178,13 @@ __device__ void split_fx(int* Ji, int k0, float ax, float ay, float az, float dx
     }
 }
 
-template <int S, int NT, bool CU>
+// G: slot p of the sorted order holds particle perm[p] of `pin` (the sort
+// computed ranks only); its updated record goes to slot p of `ps`, read with
+// element loads.  Otherwise pin is ps and the groups are updated in place.
+template <int S, int NT, bool CU, bool G>
 __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
-    k_push_g(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<float> ps, XQueue<float> xq,
+    k_push_g(const __grid_constant__ CUtensorMap tmEB, PushParams pp, PStore<float> ps, PStore<float> pin,
+             const int* __restrict__ perm, XQueue<float> xq,
              const Chunk* __restrict__ chunks, const int* __restrict__ nchunks, double* __restrict__ J,
              double* __restrict__ ek_part, int* __restrict__ err) {
     constexpr int T = S + 4, T3 = T * T * T, TJ = S + 3, TJ3 = TJ * TJ * TJ;
@@ -276,7 +280,25 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
 #pragma unroll
             for (int j = 0; j < PG; ++j) el(c4, j) = INACTIVE;
             VecF fx4{}, fy4{}, fz4{}, ux4{}, uy4{}, uz4{}, w4{};
-            if (gv) {
+            VecI id4{};
+            if (G && gv) {
+#pragma unroll
+                for (int j = 0; j < PG; ++j) {
+                    const int p = p0 + j;
+                    if (p >= start && p < end) {
+                        const int q = perm[p];
+                        el(c4, j) = pin.cell[q];
+                        el(fx4, j) = pin.off[0][q];
+                        el(fy4, j) = pin.off[1][q];
+                        el(fz4, j) = pin.off[2][q];
+                        el(ux4, j) = pin.u[0][q];
+                        el(uy4, j) = pin.u[1][q];
+                        el(uz4, j) = pin.u[2][q];
+                        el(w4, j) = pin.w[q];
+                        el(id4, j) = pin.id[q];
+                    }
+                }
+            } else if (gv) {
                 c4 = *reinterpret_cast<const VecI*>(ps.cell + p0);
                 fx4 = *reinterpret_cast<const VecF*>(ps.off[0] + p0);
                 fy4 = *reinterpret_cast<const VecF*>(ps.off[1] + p0);
@@ -449,6 +471,10 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                     *reinterpret_cast<VecF*>(ps.u[0] + p0) = ux4;
                     *reinterpret_cast<VecF*>(ps.u[1] + p0) = uy4;
                     *reinterpret_cast<VecF*>(ps.u[2] + p0) = uz4;
+                    if (G) {
+                        *reinterpret_cast<VecF*>(ps.w + p0) = w4;
+                        *reinterpret_cast<VecI*>(ps.id + p0) = id4;
+                    }
                 } else {
 #pragma unroll
                     for (int j = 0; j < PG; ++j) {
@@ -461,6 +487,10 @@ __global__ void __launch_bounds__(NT, PICGB_PUSHG_MINB)
                             ps.u[0][p] = el(ux4, j);
                             ps.u[1][p] = el(uy4, j);
                             ps.u[2][p] = el(uz4, j);
+                            if (G) {
+                                ps.w[p] = el(w4, j);
+                                ps.id[p] = el(id4, j);
+                            }
                         }
                     }
                 }
@@ -523,32 +553,44 @@ size_t push32_smem_bytes() {
 template <int S>
 cudaError_t push32_setup(int* blocks_per_sm) {
     const int sm = (int)push32_smem_bytes<S>();
-    cudaError_t e = cudaFuncSetAttribute(k_push_g<S, PUSH32_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_push_g<S, PUSH32_NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = cudaSuccess;
+    for (auto f : {k_push_g<S, PUSH32_NT, true, false>, k_push_g<S, PUSH32_NT, false, false>,
+                   k_push_g<S, PUSH32_NT, true, true>, k_push_g<S, PUSH32_NT, false, true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push_g<S, PUSH32_NT, false>, PUSH32_NT, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push_g<S, PUSH32_NT, false, false>,
+                                                         PUSH32_NT, sm);
 }
 
+// perm null: the particles are updated in place in ps.  Otherwise slot i of
+// ps receives particle perm[i] of pin, updated (the store's two buffers).
 template <int S>
 cudaError_t push32_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp,
-                          const PStore<float>& ps, const XQueue<float>& xq, const Chunk* chunks, const int* nchunks,
-                          double* J, double* ek_part, int* err) {
+                          const PStore<float>& ps, const PStore<float>& pin, const int* perm,
+                          const XQueue<float>& xq, const Chunk* chunks, const int* nchunks, double* J,
+                          double* ek_part, int* err) {
     const bool cubic = pp.g.d[0] == pp.g.d[1] && pp.g.d[1] == pp.g.d[2];
-    if (cubic)
-        k_push_g<S, PUSH32_NT, true><<<grid, PUSH32_NT, push32_smem_bytes<S>(), st>>>(tm, pp, ps, xq, chunks, nchunks,
-                                                                                     J, ek_part, err);
+    const size_t sm = push32_smem_bytes<S>();
+    if (cubic && perm)
+        k_push_g<S, PUSH32_NT, true, true><<<grid, PUSH32_NT, sm, st>>>(tm, pp, ps, pin, perm, xq, chunks, nchunks, J,
+                                                                       ek_part, err);
+    else if (cubic)
+        k_push_g<S, PUSH32_NT, true, false><<<grid, PUSH32_NT, sm, st>>>(tm, pp, ps, ps, nullptr, xq, chunks, nchunks,
+                                                                        J, ek_part, err);
+    else if (perm)
+        k_push_g<S, PUSH32_NT, false, true><<<grid, PUSH32_NT, sm, st>>>(tm, pp, ps, pin, perm, xq, chunks, nchunks,
+                                                                        J, ek_part, err);
     else
-        k_push_g<S, PUSH32_NT, false><<<grid, PUSH32_NT, push32_smem_bytes<S>(), st>>>(tm, pp, ps, xq, chunks,
-                                                                                      nchunks, J, ek_part, err);
+        k_push_g<S, PUSH32_NT, false, false><<<grid, PUSH32_NT, sm, st>>>(tm, pp, ps, ps, nullptr, xq, chunks,
+                                                                         nchunks, J, ek_part, err);
     return cudaGetLastError();
 }
 
 #define PICGB_PUSH32_INST(S)                                                                                     \
     template cudaError_t push32_setup<S>(int*);                                                                  \
     template cudaError_t push32_launch<S>(int, cudaStream_t, const CUtensorMap&, const PushParams&,              \
-                                          const PStore<float>&, const XQueue<float>&, const Chunk*, const int*,  \
-                                          double*, double*, int*);
+                                          const PStore<float>&, const PStore<float>&, const int*,                \
+                                          const XQueue<float>&, const Chunk*, const int*, double*, double*, int*);
 PICGB_PUSH32_INST(4)
 PICGB_PUSH32_INST(8)
 

@@ -449,9 +449,9 @@ __global__ void __launch_bounds__(PIPE_NT) k_sort_scatter_pipe(PStore<R> src, PS
 
 // Ranks only: each active particle's destination slot, as perm[slot] = its
 // index in the current store (one atomic per run of equal keys in consecutive
-// lanes).  The FP64 particle kernel then reads particle perm[i] and writes it
-// to slot i of the other buffer, so the particles move once per step instead
-// of twice (scatter, then push in place).
+// lanes).  The particle kernel then reads particle perm[i] and writes it to
+// slot i of the other buffer, so the particles move once per step instead of
+// twice (scatter, then push in place).
 template <class R>
 __global__ void __launch_bounds__(SORT_NT) k_sort_rank(PStore<R> ps, const long long* __restrict__ n_cur,
                                                       const long long* __restrict__ n_next, GridDev g,
@@ -525,6 +525,8 @@ cudaError_t sort_rank_launch(cudaStream_t st, int nsm, const GridDev& g, PStore<
 
 template cudaError_t sort_rank_launch<double>(cudaStream_t, int, const GridDev&, PStore<double>, const long long*,
                                               long long*, int*, int*, int*, int*, Chunk*, int*, int*);
+template cudaError_t sort_rank_launch<float>(cudaStream_t, int, const GridDev&, PStore<float>, const long long*,
+                                             long long*, int*, int*, int*, int*, Chunk*, int*, int*);
 
 template cudaError_t sort_launch<double>(cudaStream_t, int, const GridDev&, PStore<double>, PStore<double>,
                                          const long long*, long long*, int*, int*, int*, int*, Chunk*, int*, int*);

@@ -74,8 +74,8 @@ struct Store {
 
 struct Species {
     double q = 0, m = 1;
-    // FP64: destination permutation of the last ranks-only sort (cap ints); the
-    // next particle kernel moves the store through it into the other buffer
+    // destination permutation of the last ranks-only sort (cap ints); the next
+    // particle kernel moves the store through it into the other buffer
     int* d_perm = nullptr;
     bool perm_pending = false;
     bool immobile = false;         // neutralising background: no particles stored
@@ -348,17 +348,23 @@ int sort_species(pic_ctx* c, Species& s) {
     return PIC_OK;
 }
 
-// The sort before a step of the FP64 cloud-in-cell path: ranks only (count,
+// The sort before a step of the cloud-in-cell paths: ranks only (count,
 // scans, chunk table, destination permutation); the particle kernel that
 // follows moves the particles through the permutation into the other buffer.
+template <class R>
+int sort_species_ranks(pic_ctx* c, Species& s) {
+    Store<R>& st = store_of<R>(s);
+    const cudaError_t e = sort_rank_launch<R>(c->st, c->nsm, c->g, st.a(), s.d_n, s.d_n + 1, c->d_counts, c->d_cursor,
+                                              c->d_tile_sum, s.d_bin_start, s.d_chunks, s.d_nchunks, s.d_perm);
+    if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "sort launch: %s", cudaGetErrorString(e));
+    return PIC_OK;
+}
+
 int sort_all_ranks(pic_ctx* c) {
     for (auto& s : c->sp) {
         if (s.immobile) continue;
-        Store<double>& st = s.s64;
-        cudaError_t e = sort_rank_launch<double>(c->st, c->nsm, c->g, st.a(), s.d_n, s.d_n + 1, c->d_counts,
-                                                 c->d_cursor, c->d_tile_sum, s.d_bin_start, s.d_chunks, s.d_nchunks,
-                                                 s.d_perm);
-        if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "sort launch: %s", cudaGetErrorString(e));
+        const int r = c->mixed ? sort_species_ranks<float>(c, s) : sort_species_ranks<double>(c, s);
+        if (r) return r;
         c->launches += 5;
         s.perm_pending = true;
         CUDA_TRY(c, cudaMemcpyAsync(s.d_n, s.d_n + 1, sizeof(long long), cudaMemcpyDeviceToDevice, c->st));
@@ -469,10 +475,19 @@ int push_species(pic_ctx* c, Species& s) {
         }
     } else {
         if (c->adaptive) pp.drift = c->d_drift + std::min(c->since_sort, DRIFT_ROWS - 1);
+        const bool g = s.perm_pending;
+        PStore<R>& out = g ? store_of<R>(s).b() : ps;
+        const int* perm = g ? s.d_perm : nullptr;
         if (S == 4)
-            e = push32_launch<4>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+            e = push32_launch<4>(c->push_grid, c->st, tm, pp, out, ps, perm, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
+                                 c->d_err);
         if (S == 8)
-            e = push32_launch<8>(c->push_grid, c->st, tm, pp, ps, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek, c->d_err);
+            e = push32_launch<8>(c->push_grid, c->st, tm, pp, out, ps, perm, xq, s.d_chunks, s.d_nchunks, c->J, s.d_ek,
+                                 c->d_err);
+        if (g && e == cudaSuccess) {
+            store_of<R>(s).cur ^= 1;
+            s.perm_pending = false;
+        }
     }
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "push launch: %s", cudaGetErrorString(e));
     c->launches += 1;
@@ -503,7 +518,7 @@ int alloc_store(pic_ctx* c, Species& s, Store<R>& st, long long cap) {
         if (!r) r = dalloc(c, s.allocs, &p.id, cap);
         if (r) return r;
     }
-    if (sizeof(R) == 8) {
+    {
         int r = dalloc(c, s.allocs, &s.d_perm, cap);
         if (r) return r;
     }
@@ -1454,8 +1469,8 @@ int pic_step(pic_ctx* c, int nsteps) {
         if (rd) return rd;
         if (due) {
             stage_begin(c, 2, &e0);
-            // FP64 cloud-in-cell: the particle kernel below moves the particles
-            const bool ranks = !c->mixed && c->desc.form_factor != 2;
+            // cloud-in-cell: the particle kernel below moves the particles
+            const bool ranks = c->desc.form_factor != 2;
             int r = ranks ? sort_all_ranks(c) : sort_all(c);
             if (r) return r;
             stage_end(c, 2, e0);

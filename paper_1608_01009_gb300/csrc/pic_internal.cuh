@@ -331,7 +331,8 @@ template <int S>
 cudaError_t push32_setup(int* blocks_per_sm);
 template <int S>
 cudaError_t push32_launch(int grid, cudaStream_t st, const CUtensorMap& tm, const PushParams& pp,
-                          const PStore<float>& ps, const XQueue<float>& xq, const Chunk* chunks, const int* nchunks,
-                          double* J, double* ek_part, int* err);
+                          const PStore<float>& ps, const PStore<float>& pin, const int* perm,
+                          const XQueue<float>& xq, const Chunk* chunks, const int* nchunks, double* J,
+                          double* ek_part, int* err);
 
 }  // namespace picgb
