@@ -475,6 +475,37 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_rank(PStore<R> ps, const long 
     }
 }
 
+// Apply a pending permutation without a particle step: slot i of dst gets
+// particle perm[i] of src, every field (for callers that read or replace the
+// store before the next particle kernel would have moved it).
+template <class R>
+__global__ void __launch_bounds__(SORT_NT) k_apply_perm(PStore<R> src, PStore<R> dst, const long long* __restrict__ n,
+                                                       const int* __restrict__ perm) {
+    const long long N = *n;
+    for (long long i = (long long)blockIdx.x * SORT_NT + threadIdx.x; i < N; i += (long long)gridDim.x * SORT_NT) {
+        const int q = perm[i];
+        dst.cell[i] = src.cell[q];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dst.off[a][i] = src.off[a][q];
+            dst.u[a][i] = src.u[a][q];
+        }
+        dst.w[i] = src.w[q];
+        dst.id[i] = src.id[q];
+    }
+}
+
+template <class R>
+cudaError_t apply_perm_launch(cudaStream_t st, int nsm, PStore<R> src, PStore<R> dst, const long long* n,
+                              const int* perm) {
+    k_apply_perm<R><<<nsm * 8, SORT_NT, 0, st>>>(src, dst, n, perm);
+    return cudaGetLastError();
+}
+template cudaError_t apply_perm_launch<double>(cudaStream_t, int, PStore<double>, PStore<double>, const long long*,
+                                               const int*);
+template cudaError_t apply_perm_launch<float>(cudaStream_t, int, PStore<float>, PStore<float>, const long long*,
+                                              const int*);
+
 int sort_grid(int nsm) { return nsm * 8; }
 
 long long sort_tiles(long long nkeys) { return (nkeys + SCAN_TILE - 1) / SCAN_TILE; }

@@ -26,6 +26,8 @@ cudaError_t sort_launch(cudaStream_t, int, const GridDev&, PStore<R>, PStore<R>,
 template <class R>
 cudaError_t sort_rank_launch(cudaStream_t, int, const GridDev&, PStore<R>, const long long*, long long*, int*, int*,
                              int*, int*, Chunk*, int*, int*);
+template <class R>
+cudaError_t apply_perm_launch(cudaStream_t, int, PStore<R>, PStore<R>, const long long*, const int*);
 long long sort_tiles(long long nkeys);
 long long sort_tile_scratch(long long nkeys);
 template <class R>
@@ -370,12 +372,36 @@ int sort_all_ranks(pic_ctx* c) {
         CUDA_TRY(c, cudaMemcpyAsync(s.d_n, s.d_n + 1, sizeof(long long), cudaMemcpyDeviceToDevice, c->st));
     }
     c->since_sort = 0;
+    c->vsum0 = 0.0;
+    if (c->d_drift) CUDA_TRY(c, cudaMemsetAsync(c->d_drift, 0, DRIFT_ROWS * sizeof(unsigned), c->st));
+    return PIC_OK;
+}
+
+// Move the records of every species with a pending permutation into sorted
+// order now (for the entry points that read, sort or replace the store before
+// a particle step would have moved them).
+int materialize(pic_ctx* c) {
+    for (auto& s : c->sp) {
+        if (!s.perm_pending) continue;
+        cudaError_t e;
+        if (c->mixed) {
+            e = apply_perm_launch<float>(c->st, c->nsm, s.s32.a(), s.s32.b(), s.d_n, s.d_perm);
+            if (e == cudaSuccess) s.s32.cur ^= 1;
+        } else {
+            e = apply_perm_launch<double>(c->st, c->nsm, s.s64.a(), s.s64.b(), s.d_n, s.d_perm);
+            if (e == cudaSuccess) s.s64.cur ^= 1;
+        }
+        if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "permutation: %s", cudaGetErrorString(e));
+        c->launches += 1;
+        s.perm_pending = false;
+    }
     return PIC_OK;
 }
 
 int sort_all(pic_ctx* c) {
+    int rm = materialize(c);  // a full sort starts from the records in sorted order
+    if (rm) return rm;
     for (auto& s : c->sp) {
-        s.perm_pending = false;  // a full sort rebuilds the order from the current buffer
         if (s.immobile) continue;  // empty store, never pushed
         int r = c->mixed ? sort_species<float>(c, s) : sort_species<double>(c, s);
         if (r) return r;
@@ -586,6 +612,10 @@ int refresh_wmax(pic_ctx* c, Species& s) {
 
 // (Re)load the particles of species s from FP64 arrays (host or device).
 int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src, bool device) {
+    {
+        const int rm = materialize(c);  // the other species are re-sorted below
+        if (rm) return rm;
+    }
     if (n < 0 || n >= (1LL << 31) - 1) return fail(c, PIC_ERR_ARG, "particle count %lld out of range", n);
     for (int k = 0; k < 7 && n > 0; ++k)
         if (!src[k]) return fail(c, PIC_ERR_ARG, "null particle array %d", k);
@@ -617,9 +647,11 @@ int load_particles(pic_ctx* c, Species& s, long long n, const double* const* src
     c->launches += n > 0 ? 1 : 0;
     if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "load: %s", cudaGetErrorString(e));
     // bin the new particles; the other species are re-sorted too, so that every
-    // species starts the next sort interval together
-    r = sort_all(c);
-    if (!r) r = refresh_wmax(c, s);
+    // species starts the next sort interval together.  On the cloud-in-cell paths
+    // ranks only: the next particle step moves the records (every other reader
+    // of the store applies the permutation first, see materialize)
+    r = refresh_wmax(c, s);
+    if (!r) r = c->desc.form_factor != 2 ? sort_all_ranks(c) : sort_all(c);
     c->energy_fresh = false;
     return r;
 }
@@ -759,6 +791,10 @@ int device_status(pic_ctx* c) {
 template <class R>
 int get_particles_impl(pic_ctx* c, int species, int64_t cap, int64_t* n, int64_t* id, double* const* dst,
                        bool device) {
+    {
+        const int rm = materialize(c);
+        if (rm) return rm;
+    }
     Species& s = c->sp[species];
     PStore<R>& ps = store_of<R>(s).a();
     CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->st));
@@ -873,6 +909,10 @@ int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
     if (nsteps < 1 || K < 1) return fail(c, PIC_ERR_ARG, "nsteps and ckpt_every must be >= 1");
     if (c->desc.form_factor == 2)
         return fail(c, PIC_ERR_STATE, "the differentiable path implements the cloud-in-cell form factor only");
+    {
+        const int rm = materialize(c);  // the tape starts from the store in sorted order
+        if (rm) return rm;
+    }
     Tape& t = c->tape;
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     t.release();
@@ -1411,6 +1451,10 @@ int pic_count_particles(pic_ctx* c, int species, int64_t* n) {
     if (!c) return PIC_ERR_ARG;
     if (!n || species < 0 || species >= (int)c->sp.size()) return fail(c, PIC_ERR_ARG, "bad species or null n");
     CUDA_TRY(c, cudaSetDevice(c->dev));
+    {
+        const int rm = materialize(c);
+        if (rm) return rm;
+    }
     CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->st));
     Species& s = c->sp[species];
     cudaError_t e = c->mixed ? count_launch<float>(c->st, c->nsm, s.s32.a(), s.d_n, c->d_counter)
@@ -1471,7 +1515,8 @@ int pic_step(pic_ctx* c, int nsteps) {
             stage_begin(c, 2, &e0);
             // cloud-in-cell: the particle kernel below moves the particles
             const bool ranks = c->desc.form_factor != 2;
-            int r = ranks ? sort_all_ranks(c) : sort_all(c);
+            int r = materialize(c);  // a permutation still pending (a load's) is applied first
+            if (!r) r = ranks ? sort_all_ranks(c) : sort_all(c);
             if (r) return r;
             stage_end(c, 2, e0);
         }
@@ -1514,6 +1559,8 @@ int pic_energy(pic_ctx* c, double* wf, double* wk) {
     if (!wf || !wk) return fail(c, PIC_ERR_ARG, "null output");
     CUDA_TRY(c, cudaSetDevice(c->dev));
     if (!c->energy_fresh) {
+        const int rm = materialize(c);  // the kinetic energy reads the store
+        if (rm) return rm;
         CUDA_TRY(c, field_energy_launch(c->st, c->EB, c->g, c->d_wf));
         c->launches += 1;
         for (auto& s : c->sp) {
@@ -1576,6 +1623,10 @@ int pic_get_state(pic_ctx* c, void* blob, int64_t* bytes) {
     if (!c) return PIC_ERR_ARG;
     if (!bytes) return fail(c, PIC_ERR_ARG, "null size");
     CUDA_TRY(c, cudaSetDevice(c->dev));
+    {
+        const int rm = materialize(c);  // the blob holds the store in sorted order
+        if (rm) return rm;
+    }
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     std::vector<long long> n(c->sp.size());
     std::vector<int> nch(c->sp.size());
@@ -1648,6 +1699,11 @@ int pic_set_state(pic_ctx* c, const void* blob, int64_t bytes) {
     if (!c) return PIC_ERR_ARG;
     if (!blob || bytes < (int64_t)sizeof(StateHeader)) return fail(c, PIC_ERR_ARG, "null or short state blob");
     CUDA_TRY(c, cudaSetDevice(c->dev));
+    {
+        // a refused blob leaves the context as it was, in sorted order
+        const int rm = materialize(c);
+        if (rm) return rm;
+    }
     Cursor cur{const_cast<unsigned char*>(static_cast<const unsigned char*>(blob)), (size_t)bytes};
     unsigned char* at;
     cur.take(sizeof(StateHeader), &at);
