@@ -11,6 +11,9 @@
   electrons plus an immobile background equals the electron-only run.
 * A species that grows beyond its store (re-allocation) uploads whole, from
   pinned or pageable host arrays.
+* Right after a load (its sort leaves the record moves to the next particle
+  step), reading the particles, counting them, the kinetic energy, a
+  checkpoint and the tape all see the loaded particles.
 """
 import numpy as np
 import pytest
@@ -258,3 +261,39 @@ def test_species_grows_through_pageable_uploads():
     assert PT.rel_err(a.get_fields()[0], b.get_fields()[0]) <= 1e-13
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(P.FP64, 1e-15), (P.MIXED, 1e-7)])
+def test_every_reader_sees_a_load_before_its_first_step(precision, tol):
+    # a load bins its particles by ranks only and leaves the record moves to the next particle
+    # step; reading, counting, energy, checkpoint and the tape must apply that permutation first
+    import oracle as O
+    wl = _two_species()
+    for reader in ("particles", "count", "energy", "state", "tape"):
+        sim = PT.make_sim(wl, precision=precision)
+        if reader == "particles":
+            for s, sp in enumerate(wl.species):
+                p = sim.get_particles(s)
+                o = np.argsort(p["id"])
+                for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+                    assert PT.rel_err(p[k][o], getattr(sp, k)) <= tol, (reader, k)
+        elif reader == "count":
+            assert [sim.count(s) for s in range(2)] == [sp.n for sp in wl.species]
+        elif reader == "energy":
+            wk = sim.energy()[1]
+            ref = O.Oracle.from_workload(wl).kinetic_energy()
+            assert abs(wk - ref) <= 10 * tol * abs(ref)
+        elif reader == "state":
+            blob = sim.get_state()
+            b = PT.make_sim(W.uniform_plasma((16, 8, 12), 1, 0.05, 0.0, seed=1), precision=precision)
+            b.set_state(blob)
+            sim.step(3)
+            b.step(3)
+            _compare(_snapshot(b, 2), _snapshot(sim, 2), 1e-12 if precision == P.FP64 else 1e-6)
+            b.close()
+        elif reader == "tape" and precision == P.FP64:
+            wk = sim.tape_forward(2, 1)
+            ora = O.Oracle.from_workload(wl)
+            ora.step(2)
+            assert abs(wk - ora.kinetic_energy()) <= 1e-12 * abs(wk)
+        sim.close()
