@@ -44,8 +44,15 @@ __device__ __forceinline__ int cell_key(const GridDev& g, int cp) {
     return (((sc << sh) + (iz & m)) << (2 * sh)) + ((iy & m) << sh) + (ix & m);
 }
 
-// Lane-interleaved groups of U x 32 particles per warp and iteration.
-constexpr int COUNT_U = 4;
+// Lane-interleaved groups of U x 32 particles per warp and iteration (U
+// independent loads and atomics in flight per lane).
+#ifndef PICGB_COUNT_U
+#define PICGB_COUNT_U 4
+#endif
+#ifndef PICGB_RANK_U
+#define PICGB_RANK_U 4
+#endif
+constexpr int COUNT_U = PICGB_COUNT_U, RANK_U = PICGB_RANK_U;
 
 // Runs of equal keys in consecutive lanes (the store is sorted by key up to
 // the particles that changed cell since the last sort): `head` is the first
@@ -459,19 +466,27 @@ __global__ void __launch_bounds__(SORT_NT) k_sort_rank(PStore<R> ps, const long 
     const long long N = *n_cur, M = *n_next;
     const long long nkeys = (long long)g.n[0] * g.n[1] * g.n[2];
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * SORT_NT;
-    for (long long b = (long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31); b < N; b += stride) {
-        const long long p = b + lane;
-        const int cp = p < N ? ps.cell[p] : INACTIVE;
-        int key = cp < 0 ? -1 : cell_key(g, cp);
-        if (key >= 0 && !in_range(key, nkeys)) key = -1;  // debug build only
-        int head, len;
-        key_run(key, lane, head, len);
-        int s0 = 0;
-        if (lane == head && key >= 0) s0 = atomicAdd(&cursor[key], len);
-        s0 = __shfl_sync(0xffffffffu, s0, head);
-        const long long slot = (long long)s0 + (lane - head);
-        if (key >= 0 && in_range(slot, M)) perm[slot] = (int)p;
+    const long long stride = (long long)gridDim.x * SORT_NT * RANK_U;
+    for (long long b = ((long long)blockIdx.x * SORT_NT + (threadIdx.x & ~31)) * RANK_U; b < N; b += stride) {
+        int key[RANK_U], head[RANK_U], len[RANK_U], s0[RANK_U];
+#pragma unroll
+        for (int i = 0; i < RANK_U; ++i) {
+            const long long p = b + i * 32 + lane;
+            const int cp = p < N ? ps.cell[p] : INACTIVE;
+            key[i] = cp < 0 ? -1 : cell_key(g, cp);
+            if (key[i] >= 0 && !in_range(key[i], nkeys)) key[i] = -1;  // debug build only
+        }
+#pragma unroll
+        for (int i = 0; i < RANK_U; ++i) {
+            key_run(key[i], lane, head[i], len[i]);
+            s0[i] = lane == head[i] && key[i] >= 0 ? atomicAdd(&cursor[key[i]], len[i]) : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < RANK_U; ++i) {
+            const int base = __shfl_sync(0xffffffffu, s0[i], head[i]);
+            const long long slot = (long long)base + (lane - head[i]);
+            if (key[i] >= 0 && in_range(slot, M)) perm[slot] = (int)(b + i * 32 + lane);
+        }
     }
 }
 
