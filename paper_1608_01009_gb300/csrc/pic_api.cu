@@ -350,9 +350,10 @@ int sort_species(pic_ctx* c, Species& s) {
     return PIC_OK;
 }
 
-// The sort before a step of the cloud-in-cell paths: ranks only (count,
-// scans, chunk table, destination permutation); the particle kernel that
-// follows moves the particles through the permutation into the other buffer.
+// The cloud-in-cell paths' sort (before a step, and after a load): ranks only
+// (count, scans, chunk table, destination permutation); the next particle
+// kernel launch moves the particles through the permutation into the other
+// buffer, or materialize() does when another entry point needs them first.
 template <class R>
 int sort_species_ranks(pic_ctx* c, Species& s) {
     Store<R>& st = store_of<R>(s);
@@ -399,7 +400,7 @@ int materialize(pic_ctx* c) {
 }
 
 int sort_all(pic_ctx* c) {
-    int rm = materialize(c);  // a full sort starts from the records in sorted order
+    int rm = materialize(c);  // a full sort reads the current buffer: no permutation may be pending
     if (rm) return rm;
     for (auto& s : c->sp) {
         if (s.immobile) continue;  // empty store, never pushed
