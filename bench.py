@@ -343,14 +343,16 @@ def mixed_vs_fp64(torch, pic, wl, checkpoints=(100, 200)):
             "target": "field energy <= 1e-5 relative after 100 steps"}
 
 
-def time_laser_ramp(torch, pic, W, total=500, adj=50, ck=25):
+def time_laser_ramp(torch, pic, W, total=500, adj=50, ck=50):
     """The large laser-plasma workload c5 (256x128x128, 134.2 M electrons over a
     density ramp, a0 = 3 Gaussian pulse, x absorbing): the mixed-precision
     forward for the first total - adj steps (3 of them untimed warm-up), then
     the differentiable FP64 path for the final adj steps and its adjoint.
-    Checkpoint every ck steps: with 25 the tape holds 2 checkpoints + the 25
-    step states of the last segment, 27 FP64 states of 7 GB each, and only the
-    first segment is recomputed.  The adjoint is set against the checkpointed
+    Checkpoint every ck steps: with 50 the tape is one segment (a whole FP64
+    state of 7 GB, the 50 steps' momenta, 3.2 GB each, and the positions and
+    flags of every 8th step), so nothing is recomputed; if that does not fit in
+    device memory the run takes ck = 25 and recomputes the first segment.
+    The adjoint is set against the checkpointed
     forward it reverses and against plain steps of the same state: FP64
     pic_step steps (a context loaded with the state at step total - adj) and
     the mixed context's own steps."""
@@ -388,7 +390,15 @@ def time_laser_ramp(torch, pic, W, total=500, adj=50, ck=25):
     torch.cuda.empty_cache()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    wk_end = sim.tape_forward(adj, ck)
+    try:
+        wk_end = sim.tape_forward(adj, ck)
+    except pic.PicError as e:
+        if e.code != -3 or ck <= 25:  # PIC_ERR_OOM
+            raise
+        ck = 25
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        wk_end = sim.tape_forward(adj, ck)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     dE, dB = sim.tape_backward(1.0)
@@ -411,9 +421,9 @@ def time_laser_ramp(torch, pic, W, total=500, adj=50, ck=25):
                         "adjoint_vs_fast_forward": bwd / fast_fp64_s,
                         "adjoint_vs_fast_mixed_forward": bwd / (mixed_step_s * adj),
                         "W_K_final": wk_end, "grad_E_norm": gnorm[0], "grad_B_norm": gnorm[1],
-                        "note": "backward = segment replay (recomputation) + adjoint kernels; "
-                                "adjoint_vs_fast_forward divides by FP64 pic_step steps of the same state, "
-                                "the ratio judged against the 3x target"},
+                        "note": "backward = segment replay (recomputation, none with one segment), position "
+                                "rebuilds + adjoint kernels; adjoint_vs_fast_forward divides by FP64 pic_step "
+                                "steps of the same state, the ratio judged against the 3x target"},
             "input_generation_s": gen_s}
 
 

@@ -280,15 +280,20 @@ PIC_API int pic_launch_count(pic_ctx* ctx, int64_t* n, int reset);
  * gather, Boris push, Villasenor-Buneman deposit, Yee FDTD; Sec. 2-3), with
  * the particles kept in id order and no supercell sort, so that any segment
  * can be replayed exactly -- saving the FP64 state every `ckpt_every` steps in
- * library-owned device memory.  *wk receives the final kinetic energy
+ * library-owned device memory, and recording the last segment's steps (each
+ * step's momenta, and the positions and active flags of every
+ * ceil(sqrt(ckpt_every))-th step, from which the others are rebuilt exactly:
+ * about 24 + 28 / sqrt(ckpt_every) bytes per particle and step, against 52 for
+ * a whole state).  *wk receives the final kinetic energy
  * W_K = sum m w (gamma - 1).  The context continues from the final state.
+ * PIC_ERR_OOM if the tape does not fit in device memory (nothing is kept).
  *
  * pic_tape_backward then computes the gradient of
  *     L = wk_weight * W_K(final) + <gE, E(final)> + <gB, B(final)>
  * with respect to the fields at the start of the tape: for each checkpoint
  * segment in reverse it restores the checkpoint, recomputes the segment while
- * keeping every step's state, and runs the adjoint kernels backwards through
- * it.  gE, gB: unpadded device arrays or NULL (zero); dE0, dB0: unpadded
+ * recording its steps (the last segment was recorded by the forward), and runs
+ * the adjoint kernels backwards through it.  gE, gB: unpadded device arrays or NULL (zero); dE0, dB0: unpadded
  * device arrays that receive dL/dE(start), dL/dB(start), or NULL.  Both calls
  * synchronise.  pic_tape_particle_grad then copies dL/d(x, y, z, ux, uy, uz)
  * of the starting particles of a species, in id order (device arrays of the

@@ -254,6 +254,7 @@ __device__ void deposit_global(double* J, const GridDev& g, const int cell0[3], 
 __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int cell0[3], const double a[3],
                                 const double d[3], const double Q[3], double la[3], double ld[3]) {
     const Pieces P = pieces_of(a, d);
+    const double Q12[3] = {Q[0] * (1.0 / 12.0), Q[1] * (1.0 / 12.0), Q[2] * (1.0 / 12.0)};
     double lt[3] = {0.0, 0.0, 0.0};  // cotangents of the sorted crossing parameters
     double ta = 0.0;
     for (int s = 0; s < P.n; ++s) {
@@ -270,7 +271,7 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
             }
             double m[3];
             for (int c = 0; c < 3; ++c) m[c] = fma(0.5, dd[c], pa[c]);
-            double lpa[3] = {0, 0, 0}, ldd[3] = {0, 0, 0};
+            double lm[3] = {0, 0, 0}, ldd[3] = {0, 0, 0};  // cotangents of the midpoint and of dd
             for (int c = 0; c < 3; ++c) {
                 const int p = (c + 1) % 3, r = (c + 2) % 3;
                 const double* Lc = LJ + (long long)c * g.P;
@@ -294,11 +295,21 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
                 const double S = fma(m[r], Dr, Sp0);
                 const double Dp = fma(m[r], K, a0);
                 const double qd = Q[c] * dd[c];
-                ldd[c] += Q[c] * (S + K * dd[p] * dd[r] * (1.0 / 12.0));
-                lpa[p] += qd * Dp;
-                lpa[r] += qd * Dr;
-                ldd[p] += 0.5 * qd * Dp + qd * K * dd[r] * (1.0 / 12.0);
-                ldd[r] += 0.5 * qd * Dr + qd * K * dd[p] * (1.0 / 12.0);
+                const double kq = K * Q12[c];  // Q_c K / 12
+                const double kk = kq * dd[c];  // Q_c d_c K / 12
+                // df/dd_c = Q_c (S + K d_p d_r / 12); df/dm_p = Q_c d_c Dp, df/dm_r = Q_c d_c Dr;
+                // df/dd_p = Q_c d_c K d_r / 12, df/dd_r = Q_c d_c K d_p / 12
+                ldd[c] = fma(Q[c], S, fma(kq * dd[p], dd[r], ldd[c]));
+                lm[p] = fma(qd, Dp, lm[p]);
+                lm[r] = fma(qd, Dr, lm[r]);
+                ldd[p] = fma(kk, dd[r], ldd[p]);
+                ldd[r] = fma(kk, dd[p], ldd[r]);
+            }
+            // m = pa + dd / 2
+            double lpa[3];
+            for (int c = 0; c < 3; ++c) {
+                lpa[c] = lm[c];
+                ldd[c] = fma(0.5, lm[c], ldd[c]);
             }
             // pa = a + ta d - o, dd = (tb - ta) d
             double lta = 0.0, ltb = 0.0;
@@ -320,6 +331,30 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
         la[c] -= q;
         ld[c] -= q * P.t[s];
     }
+}
+
+// Displacement d = dtd u / gamma of a step (u = u^{n+1/2}) and the new position x^{n+1} = x^n + d:
+// periodic axes wrap, and the return value says whether the particle left an absorbing axis.
+// The tape's forward step and the rebuild of positions from a checkpoint (k_tape_move) both
+// call it; the products and sums are explicitly rounded (never contracted into an FMA), so a
+// rebuilt position equals the recorded one bit for bit.
+__device__ __forceinline__ bool move_of(const double xi[3], const double u[3], const StepParams& sp, double d[3],
+                                        double x1[3]) {
+    const double gi = rsqrt_ge1(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
+    bool gone = false;
+    for (int c = 0; c < 3; ++c) {
+        d[c] = __dmul_rn(u[c], __dmul_rn(gi, sp.dtd[c]));
+        double x = __dadd_rn(xi[c], d[c]);
+        const double nc = (double)sp.g.n[c];
+        if (sp.g.bc[c] == 0) {
+            if (x < 0.0) x = __dadd_rn(x, nc);
+            if (x >= nc) x = __dadd_rn(x, -nc);
+        } else if (x < 0.0 || x >= nc) {
+            gone = true;
+        }
+        x1[c] = x;
+    }
+    return gone;
 }
 
 // One forward step of every particle.
@@ -345,32 +380,39 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, S
         const double u0[3] = {u[0], u[1], u[2]};
         boris_fwd(u0, F, F + 3, sp.qdt2m, u, bf);
     }
-    const double gi = rsqrt_ge1(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
-    double d[3], a[3];
-    int cell0[3];
-    for (int c = 0; c < 3; ++c) {
-        d[c] = u[c] * (gi * sp.dtd[c]);
-        cell0[c] = lat.c0[c];
-        a[c] = lat.f0[c];
-    }
+    double d[3], x1[3];
+    const bool gone = move_of(xi, u, sp, d, x1);
     const double w = T.w[p];
     if (w != 0.0 && sp.cq[0] != 0.0) {
         const double Q[3] = {sp.cq[0] * w, sp.cq[1] * w, sp.cq[2] * w};
-        deposit_global(J, g, cell0, a, d, Q);
+        deposit_global(J, g, lat.c0, lat.f0, d, Q);
     }
-    bool gone = false;
     for (int c = 0; c < 3; ++c) {
-        double x1 = xi[c] + d[c];
-        if (g.bc[c] == 0) {
-            if (x1 < 0.0) x1 += g.n[c];
-            if (x1 >= g.n[c]) x1 -= g.n[c];
-        } else if (x1 < 0.0 || x1 >= g.n[c]) {
-            gone = true;
-        }
-        T.xi[c][p] = x1;
+        T.xi[c][p] = x1[c];
         T.u[c][p] = u[c];
     }
     if (gone) T.act[p] = 0;
+}
+
+// Rebuild of the next position from a recorded state: src holds x^n and its active flag,
+// with src.u = u^{n+1/2} (the momentum after the step); dst.xi and dst.act receive x^{n+1} and
+// its flag, exactly as k_tape_step moves the particle (dst may alias src; dst.u is unused).
+__global__ void __launch_bounds__(TAPE_NT) k_tape_move(TapeDev src, TapeDev dst, long long n, StepParams sp) {
+    const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
+    if (p >= n) return;
+    const double xi[3] = {src.xi[0][p], src.xi[1][p], src.xi[2][p]};
+    const int act = src.act[p];
+    if (!act) {
+        if (dst.xi[0] != src.xi[0])
+            for (int c = 0; c < 3; ++c) dst.xi[c][p] = xi[c];
+        dst.act[p] = 0;
+        return;
+    }
+    const double u[3] = {src.u[0][p], src.u[1][p], src.u[2][p]};
+    double d[3], x1[3];
+    const bool gone = move_of(xi, u, sp, d, x1);
+    for (int c = 0; c < 3; ++c) dst.xi[c][p] = x1[c];
+    dst.act[p] = gone ? 0 : 1;
 }
 
 // Cotangent of the final kinetic energy: lambda_u = weight * m w u / gamma, lambda_x = 0.
@@ -390,7 +432,10 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_seed(TapeDev T, LamDev L, long
 // L holds the cotangents of x^{n+1}, u^{n+1/2} on entry and of x^n, u^{n-1/2}
 // on exit; EB = E^n, B^n; LJ = lambda_J (ghosts filled); scat receives the
 // gather cotangents lambda_E, lambda_B (padded, atomics; ghosts folded later).
-__global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp,
+#ifndef PICGB_TAPE_MINB
+#define PICGB_TAPE_MINB 2  // CTAs per SM the adjoint kernel's register budget is set for
+#endif
+__global__ void __launch_bounds__(TAPE_NT, PICGB_TAPE_MINB) k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp,
                                                          const double* __restrict__ EB, const double* __restrict__ LJ,
                                                          double* __restrict__ scat) {
     bool ok;
@@ -402,13 +447,12 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     // recompute the forward gather, with the position derivatives of each
     // interpolant from the same lerp tree: v = lerp_z(lerp_y(lerp_x(corners)))
     const Lat lat = lattices(xi);
-    double F[6], dF[6][3], fr[6][3];
+    double F[6], dF[6][3];
     int bs[6][3];
     for (int c = 0; c < 6; ++c) {
-        double v[8];
-        lattice(c, lat, bs[c], fr[c]);
+        double v[8], f[3];
+        lattice(c, lat, bs[c], f);
         corners(EB, g, c, bs[c], v);
-        const double* f = fr[c];
         const double a0 = v[1] - v[0], a1 = v[3] - v[2], a2 = v[5] - v[4], a3 = v[7] - v[6];
         const double c00 = fma(f[0], a0, v[0]), c10 = fma(f[0], a1, v[2]);
         const double c01 = fma(f[0], a2, v[4]), c11 = fma(f[0], a3, v[6]);
@@ -423,14 +467,11 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     double u1[3];
     BorisFwd bf;
     boris_fwd(u0, F, F + 3, sp.qdt2m, u1, bf);
-    const double u2p1 = fma(u1[0], u1[0], fma(u1[1], u1[1], fma(u1[2], u1[2], 1.0)));
-    const double gi = rsqrt_ge1(u2p1);
-    double d[3], a[3];
-    int cell0[3];
-    for (int c = 0; c < 3; ++c) {
-        d[c] = u1[c] * (gi * sp.dtd[c]);
-        cell0[c] = lat.c0[c];
-        a[c] = lat.f0[c];
+    const double gi = rsqrt_ge1(fma(u1[0], u1[0], fma(u1[1], u1[1], fma(u1[2], u1[2], 1.0))));
+    double d[3];
+    {
+        double x1[3];
+        move_of(xi, u1, sp, d, x1);  // the forward's displacement, bit for bit
     }
     // cotangents of the outputs
     double lx1[3] = {L.xi[0][p], L.xi[1][p], L.xi[2][p]};
@@ -440,7 +481,7 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     const double w = T.w[p];
     if (w != 0.0 && sp.cq[0] != 0.0) {
         const double Q[3] = {sp.cq[0] * w, sp.cq[1] * w, sp.cq[2] * w};
-        deposit_adjoint(LJ, g, cell0, a, d, Q, la, ld);
+        deposit_adjoint(LJ, g, lat.c0, lat.f0, d, Q, la, ld);
     }
     // move: x^{n+1} = x^n + d, d = dtd u / gamma
     double lx0[3];
@@ -458,21 +499,39 @@ __global__ void __launch_bounds__(TAPE_NT, 2) k_tape_adjoint(TapeDev T, LamDev L
     // Boris
     double lu0[3], lF[6] = {0, 0, 0, 0, 0, 0};
     boris_adjoint(bf, F + 3, sp.qdt2m, lu1, lu0, lF, lF + 3);
-    // gather: scatter lambda_F with the separable CIC weights, and the position gradient
+    // gather: scatter lambda_F with the separable CIC weights, and the position gradient.
+    // The 1-D weights (1 - f, f) come from the two lattices of each axis, and the (y, z)
+    // weight products are shared by the components on the same pair of y and z lattices
+    // (Ex; Ey and Bz; Ez and By; Bx).
+    double gl[2][3];  // 1 - f on the node / half-shifted lattice
+    for (int a = 0; a < 3; ++a) {
+        gl[0][a] = 1.0 - lat.f0[a];
+        gl[1][a] = 1.0 - lat.f1[a];
+    }
+    double yz[4][4];  // [half along y + 2 half along z][by + 2 bz]
+    for (int l = 0; l < 4; ++l) {
+        const double fy = (l & 1) ? lat.f1[1] : lat.f0[1], gy = gl[l & 1][1];
+        const double fz = (l >> 1) ? lat.f1[2] : lat.f0[2], gz = gl[l >> 1][2];
+        yz[l][0] = gy * gz;
+        yz[l][1] = fy * gz;
+        yz[l][2] = gy * fz;
+        yz[l][3] = fy * fz;
+    }
     for (int c = 0; c < 6; ++c) {
-        const double* f = fr[c];
         const double sc = lF[c];
         lx0[0] = fma(sc, dF[c][0], lx0[0]);
         lx0[1] = fma(sc, dF[c][1], lx0[1]);
         lx0[2] = fma(sc, dF[c][2], lx0[2]);
-        const double gx = 1.0 - f[0], sz0 = sc * (1.0 - f[2]), sz1 = sc * f[2];
-        const double syz[4] = {sz0 * (1.0 - f[1]), sz0 * f[1], sz1 * (1.0 - f[1]), sz1 * f[1]};
+        // half-shifted axes: E_c along c, B_c along the two others
+        const bool hx = c == 0 || c == 4 || c == 5, hy = c == 1 || c == 3 || c == 5, hz = c == 2 || c == 3 || c == 4;
+        const double s1 = sc * (hx ? lat.f1[0] : lat.f0[0]), s0 = sc * gl[hx ? 1 : 0][0];
+        const double* wyz = yz[(hy ? 1 : 0) + (hz ? 2 : 0)];
         double* S = scat + (long long)c * g.P;
         for (int q = 0; q < 4; ++q) {
             const long long o = pidx(g, bs[c][0], bs[c][1] + (q & 1), bs[c][2] + (q >> 1));
             if (!in_range(o, g.P - 1)) continue;  // debug build only: o and o + 1
-            atomicAdd(&S[o], syz[q] * gx);
-            atomicAdd(&S[o + 1], syz[q] * f[0]);
+            atomicAdd(&S[o], wyz[q] * s0);
+            atomicAdd(&S[o + 1], wyz[q] * s1);
         }
     }
     for (int c = 0; c < 3; ++c) {
@@ -691,6 +750,11 @@ static int pgrid(long long n) { return (int)((n + TAPE_NT - 1) / TAPE_NT); }
 cudaError_t tape_step_launch(cudaStream_t st, const TapeDev& T, long long n, const StepParams& sp, const double* EB,
                              double* J) {
     if (n > 0) k_tape_step<<<pgrid(n), TAPE_NT, 0, st>>>(T, n, sp, EB, J);
+    return cudaGetLastError();
+}
+
+cudaError_t tape_move_launch(cudaStream_t st, const TapeDev& src, const TapeDev& dst, long long n, const StepParams& sp) {
+    if (n > 0) k_tape_move<<<pgrid(n), TAPE_NT, 0, st>>>(src, dst, n, sp);
     return cudaGetLastError();
 }
 

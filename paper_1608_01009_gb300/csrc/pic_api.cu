@@ -50,6 +50,7 @@ constexpr int DRIFT_ROWS = 64;
 
 // differentiable path (k_adjoint.cu)
 cudaError_t tape_step_launch(cudaStream_t, const TapeDev&, long long, const StepParams&, const double*, double*);
+cudaError_t tape_move_launch(cudaStream_t, const TapeDev&, const TapeDev&, long long, const StepParams&);
 cudaError_t tape_seed_launch(cudaStream_t, const TapeDev&, const LamDev&, long long, double, double);
 cudaError_t tape_adjoint_launch(cudaStream_t, const TapeDev&, const LamDev&, long long, const StepParams&,
                                 const double*, const double*, double*);
@@ -103,27 +104,35 @@ struct Species {
 };
 
 // Recorded differentiable run: id-ordered FP64 particle states of every
-// species, checkpoints every K steps, per-step states of the segment being
-// reversed, and the cotangent buffers.
+// species, full checkpoints every K steps, and for the segment being reversed
+// the momentum of every step plus the positions and active flags of every
+// B-th step (B = ceil(sqrt(K))).  The positions of the other steps of a block
+// of B are rebuilt once, when the reverse sweep enters the block, by the
+// forward's own move (k_tape_move), bit for bit.  A step's record costs
+// 24 B per particle instead of the 52 B of a whole state, so the same memory
+// keeps about twice as many steps without a replay.
 struct TapeSpecies {
     long long n = 0;
     double* w = nullptr;
     TapeDev cur{};
     LamDev lam{};
-    std::vector<TapeDev> ck, snap;
+    std::vector<TapeDev> ck;  // whole states at the segment starts (a one-segment tape keeps none)
+    std::vector<TapeDev> us;  // u^{m-1/2} of step m of the segment (u only)
+    std::vector<TapeDev> xs;  // x^m and flags of steps m = 0, B, 2B, ... (xi and act only)
+    std::vector<TapeDev> xw;  // x^{m0 + j} and flags, j = 1..B-1, of the block rebuilt last
+    int blk = -1;             // first step m0 of that block (-1: none)
 };
 
 struct Tape {
     bool ready = false;
-    int nsteps = 0, K = 1;
-    int snap_seg = -1;  // checkpoint segment whose per-step states `snap` holds (-1: none)
+    int nsteps = 0, K = 1, B = 1;
+    int snap_seg = -1;  // checkpoint segment whose per-step records `us`, `xs`, `snapEB` hold (-1: none)
     std::vector<TapeSpecies> sp;
     std::vector<double*> ckEB, snapEB;
     double* finalEB = nullptr;
     double* L = nullptr;     // cotangents of E, B (6 padded components)
     double* LJ = nullptr;    // cotangent of J (3 padded components, ghosts filled)
     double* scat = nullptr;  // gather cotangents scattered by the particles (6 padded)
-    double* stage = nullptr; // 7 x n FP64 staging to re-load the store
     std::vector<void*> allocs;
     void release() {
         for (void* p : allocs) cudaFree(p);
@@ -131,7 +140,7 @@ struct Tape {
         sp.clear();
         ckEB.clear();
         snapEB.clear();
-        finalEB = L = LJ = scat = stage = nullptr;
+        finalEB = L = LJ = scat = nullptr;
         ready = false;
         snap_seg = -1;
     }
@@ -875,6 +884,35 @@ int alloc_tape_dev(pic_ctx* c, Tape& t, TapeDev& d, long long n, const double* w
     return r;
 }
 
+int alloc_tape_u(pic_ctx* c, Tape& t, TapeDev& d, long long n) {
+    int r = PIC_OK;
+    for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &d.u[a], (size_t)n);
+    return r;
+}
+
+int alloc_tape_x(pic_ctx* c, Tape& t, TapeDev& d, long long n, const double* w) {
+    int r = PIC_OK;
+    for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &d.xi[a], (size_t)n);
+    if (!r) r = dalloc(c, t.allocs, &d.act, (size_t)n);
+    d.w = w;
+    return r;
+}
+
+int copy_tape_u(pic_ctx* c, const TapeDev& dst, const TapeDev& src, long long n) {
+    if (n <= 0) return PIC_OK;
+    for (int a = 0; a < 3; ++a)
+        CUDA_TRY(c, cudaMemcpyAsync(dst.u[a], src.u[a], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
+int copy_tape_x(pic_ctx* c, const TapeDev& dst, const TapeDev& src, long long n) {
+    if (n <= 0) return PIC_OK;
+    for (int a = 0; a < 3; ++a)
+        CUDA_TRY(c, cudaMemcpyAsync(dst.xi[a], src.xi[a], n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CUDA_TRY(c, cudaMemcpyAsync(dst.act, src.act, n * sizeof(int), cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
 int copy_tape_dev(pic_ctx* c, const TapeDev& dst, const TapeDev& src, long long n) {
     if (n <= 0) return PIC_OK;
     for (int a = 0; a < 3; ++a) {
@@ -906,6 +944,45 @@ int tape_step(pic_ctx* c) {
     return PIC_OK;
 }
 
+// Records step m of the segment from the current state: its momentum, its
+// positions and flags when m is a multiple of B, and its fields.
+int tape_record(pic_ctx* c, int m) {
+    Tape& t = c->tape;
+    int r;
+    for (auto& ts : t.sp) {
+        ts.blk = -1;
+        if ((r = copy_tape_u(c, ts.us[m], ts.cur, ts.n))) return r;
+        if (m % t.B == 0 && (r = copy_tape_x(c, ts.xs[m / t.B], ts.cur, ts.n))) return r;
+    }
+    return copy_EB(c, t.snapEB[m], c->EB);
+}
+
+// The recorded state (x^m, u^{m-1/2}, flags) of step m of a segment of `len`
+// steps for species i.  Positions of a multiple m0 of B are read where they
+// were recorded; on entering the block m0 .. m0 + B - 1 (the reverse sweep
+// meets its last step first) the positions of its other steps are rebuilt
+// into xw by moving with the recorded momenta, x^{j+1} from x^j and u^{j+1/2}.
+int tape_state_at(pic_ctx* c, size_t i, int m, int len, TapeDev& T) {
+    Tape& t = c->tape;
+    TapeSpecies& ts = t.sp[i];
+    const int b = m / t.B, m0 = b * t.B, j = m - m0;
+    if (j > 0 && ts.blk != m0) {
+        const StepParams sp = step_params(c, c->sp[i]);
+        const int last = std::min(t.B - 1, len - 1 - m0);
+        for (int k = 1; k <= last; ++k) {
+            TapeDev src = k == 1 ? ts.xs[b] : ts.xw[k - 1];
+            for (int a = 0; a < 3; ++a) src.u[a] = ts.us[m0 + k].u[a];
+            CUDA_TRY(c, tape_move_launch(c->st, src, ts.xw[k], ts.n, sp));
+            c->launches += ts.n > 0 ? 1 : 0;
+        }
+        ts.blk = m0;
+    }
+    T = j == 0 ? ts.xs[b] : ts.xw[j];
+    for (int a = 0; a < 3; ++a) T.u[a] = ts.us[m].u[a];
+    T.w = ts.w;
+    return PIC_OK;
+}
+
 int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
     if (nsteps < 1 || K < 1) return fail(c, PIC_ERR_ARG, "nsteps and ckpt_every must be >= 1");
     if (c->desc.form_factor == 2)
@@ -921,6 +998,10 @@ int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
     t.K = K;
     const int nck = (nsteps + K - 1) / K;
     const int nsnap = K < nsteps ? K : nsteps;
+    int B = 1;
+    while (B * B < nsnap) ++B;
+    t.B = B;
+    const int nxs = (nsnap + B - 1) / B;
     const long long P6 = 6 * c->g.P;
     int r = PIC_OK;
     long long nmax = 1;
@@ -934,10 +1015,16 @@ int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
         if (!r) r = alloc_tape_dev(c, t, ts.cur, ts.n, ts.w);
         for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &ts.lam.xi[a], (size_t)ts.n);
         for (int a = 0; a < 3 && !r; ++a) r = dalloc(c, t.allocs, &ts.lam.u[a], (size_t)ts.n);
-        ts.ck.resize(nck);
-        ts.snap.resize(nsnap);
-        for (int k = 0; k < nck && !r; ++k) r = alloc_tape_dev(c, t, ts.ck[k], ts.n, ts.w);
-        for (int k = 0; k < nsnap && !r; ++k) r = alloc_tape_dev(c, t, ts.snap[k], ts.n, ts.w);
+        // a one-segment tape never replays, so it keeps no checkpoint (its records start
+        // with the whole initial state); with several, the last one serves a second backward
+        ts.ck.resize(nck > 1 ? nck : 0);
+        ts.us.resize(nsnap);
+        ts.xs.resize(nxs);
+        ts.xw.resize(B);
+        for (size_t k = 0; k < ts.ck.size() && !r; ++k) r = alloc_tape_dev(c, t, ts.ck[k], ts.n, ts.w);
+        for (int k = 0; k < nsnap && !r; ++k) r = alloc_tape_u(c, t, ts.us[k], ts.n);
+        for (int k = 0; k < nxs && !r; ++k) r = alloc_tape_x(c, t, ts.xs[k], ts.n, ts.w);
+        for (int k = 1; k < B && !r; ++k) r = alloc_tape_x(c, t, ts.xw[k], ts.n, ts.w);
         if (r) break;
         // the current (binned) store -> id order
         if (ts.n > 0) {
@@ -954,33 +1041,43 @@ int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
             if (e != cudaSuccess) return fail(c, PIC_ERR_CUDA, "tape load: %s", cudaGetErrorString(e));
         }
     }
-    t.ckEB.resize(nck);
+    t.ckEB.resize(nck > 1 ? nck : 0);
     t.snapEB.resize(nsnap);
-    for (int k = 0; k < nck && !r; ++k) r = dalloc(c, t.allocs, &t.ckEB[k], (size_t)P6);
+    for (size_t k = 0; k < t.ckEB.size() && !r; ++k) r = dalloc(c, t.allocs, &t.ckEB[k], (size_t)P6);
     for (int k = 0; k < nsnap && !r; ++k) r = dalloc(c, t.allocs, &t.snapEB[k], (size_t)P6);
     if (!r) r = dalloc(c, t.allocs, &t.finalEB, (size_t)P6);
     if (!r) r = dalloc(c, t.allocs, &t.L, (size_t)P6);
     if (!r) r = dalloc(c, t.allocs, &t.LJ, (size_t)(3 * c->g.P));
     if (!r) r = dalloc(c, t.allocs, &t.scat, (size_t)P6);
-    if (!r) r = dalloc(c, t.allocs, &t.stage, (size_t)(7 * nmax));
     if (r) {
         t.release();
         return r;
     }
+    // staging for the re-load of the store after the last step, taken before the first
+    // step (so that the tape fails before it starts) and freed on return: the backward
+    // does not hold it
+    double* stage = nullptr;
+    {
+        const cudaError_t e = cudaMalloc(&stage, (size_t)7 * nmax * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            t.release();
+            return fail(c, PIC_ERR_OOM, "tape re-load staging of %lld particles", nmax);
+        }
+    }
+    struct StageFree {
+        double* p;
+        ~StageFree() { cudaFree(p); }  // cudaFree waits for the device work that reads it
+    } stage_free{stage};
     for (int n = 0; n < nsteps; ++n) {
-        if (n % K == 0) {
+        if (n % K == 0 && nck > 1) {
             const int k = n / K;
             for (auto& ts : t.sp)
                 if ((r = copy_tape_dev(c, ts.ck[k], ts.cur, ts.n))) return r;
             if ((r = copy_EB(c, t.ckEB[k], c->EB))) return r;
         }
-        if (n / K == nck - 1) {
-            // the last segment's per-step states are kept: the backward starts there without a replay
-            const int m = n - (nck - 1) * K;
-            for (auto& ts : t.sp)
-                if ((r = copy_tape_dev(c, ts.snap[m], ts.cur, ts.n))) return r;
-            if ((r = copy_EB(c, t.snapEB[m], c->EB))) return r;
-        }
+        // the last segment's steps are recorded: the backward starts there without a replay
+        if (n / K == nck - 1 && (r = tape_record(c, n - (nck - 1) * K))) return r;
         if ((r = tape_step(c))) return r;
     }
     t.snap_seg = nck - 1;
@@ -997,7 +1094,7 @@ int tape_forward_impl(pic_ctx* c, int nsteps, int K, double* wk) {
         TapeSpecies& ts = t.sp[i];
         if (ts.n == 0) continue;
         double* dst[7];
-        for (int k = 0; k < 7; ++k) dst[k] = t.stage + (size_t)k * ts.n;
+        for (int k = 0; k < 7; ++k) dst[k] = stage + (size_t)k * ts.n;
         double** ddst = nullptr;
         CUDA_TRY(c, cudaMalloc(&ddst, sizeof dst));
         cudaError_t e = cudaMemcpyAsync(ddst, dst, sizeof dst, cudaMemcpyHostToDevice, c->st);
@@ -1032,24 +1129,35 @@ int tape_backward_impl(pic_ctx* c, double wk_weight, const double* const gE[3], 
         cudaMemcpy3DParms p = copy_params(c->g, t.L + k * c->g.P, const_cast<double*>(src), true);
         CUDA_TRY(c, cudaMemcpy3DAsync(&p, c->st));
     }
+    const int nck = (t.nsteps + t.K - 1) / t.K;
+    int r;
+    if (t.snap_seg != nck - 1) {
+        // an earlier backward replayed the first segments over the final state: replay the
+        // last segment from its checkpoint, recording its steps, to bring that state back
+        const int n0 = (nck - 1) * t.K, len = t.nsteps - n0;
+        for (auto& ts : t.sp)
+            if ((r = copy_tape_dev(c, ts.cur, ts.ck[nck - 1], ts.n))) return r;
+        if ((r = copy_EB(c, c->EB, t.ckEB[nck - 1]))) return r;
+        for (int m = 0; m < len; ++m) {
+            if ((r = tape_record(c, m))) return r;
+            if ((r = tape_step(c))) return r;
+        }
+        t.snap_seg = nck - 1;
+    }
     // seed: cotangent of the final kinetic energy
     for (size_t i = 0; i < c->sp.size(); ++i) {
         CUDA_TRY(c, tape_seed_launch(c->st, t.sp[i].cur, t.sp[i].lam, t.sp[i].n, c->sp[i].m, wk_weight));
         c->launches += 1;
     }
-    const int nck = (t.nsteps + t.K - 1) / t.K;
-    int r;
     for (int k = nck - 1; k >= 0; --k) {
         const int n0 = k * t.K, n1 = n0 + t.K < t.nsteps ? n0 + t.K : t.nsteps;
         if (t.snap_seg != k) {
-            // restore the checkpoint and replay the segment, keeping each step's state
+            // restore the checkpoint and replay the segment, recording each step
             for (auto& ts : t.sp)
                 if ((r = copy_tape_dev(c, ts.cur, ts.ck[k], ts.n))) return r;
             if ((r = copy_EB(c, c->EB, t.ckEB[k]))) return r;
             for (int m = 0; m < n1 - n0; ++m) {
-                for (auto& ts : t.sp)
-                    if ((r = copy_tape_dev(c, ts.snap[m], ts.cur, ts.n))) return r;
-                if ((r = copy_EB(c, t.snapEB[m], c->EB))) return r;
+                if ((r = tape_record(c, m))) return r;
                 if (m + 1 < n1 - n0 && (r = tape_step(c))) return r;
             }
             t.snap_seg = k;
@@ -1060,8 +1168,9 @@ int tape_backward_impl(pic_ctx* c, double wk_weight, const double* const gE[3], 
             c->launches += 6;
             for (size_t i = 0; i < c->sp.size(); ++i) {
                 const StepParams sp = step_params(c, c->sp[i]);
-                CUDA_TRY(c, tape_adjoint_launch(c->st, t.sp[i].snap[m], t.sp[i].lam, t.sp[i].n, sp, t.snapEB[m],
-                                                t.LJ, t.scat));
+                TapeDev T;
+                if ((r = tape_state_at(c, i, m, n1 - n0, T))) return r;
+                CUDA_TRY(c, tape_adjoint_launch(c->st, T, t.sp[i].lam, t.sp[i].n, sp, t.snapEB[m], t.LJ, t.scat));
                 c->launches += 1;
             }
             CUDA_TRY(c, adj_fold_add_launch(c->st, t.L, t.scat, c->g));

@@ -7,7 +7,9 @@ Checks, in order of strength:
   in dual numbers, independent of the CUDA path): the directional derivative
   of the final kinetic energy along random (E0, B0, x0, u0) directions;
 * against central finite differences of the GPU forward (h = 1e-6, 1e-6 relative);
-* checkpoint interval does not change the gradient;
+* checkpoint interval does not change the gradient, also where particles
+  leave through an absorbing face between the recorded positions, and a
+  second backward of the same tape gives the first one's gradient;
 * the torch.autograd.Function and the gradient with respect to a laser
   amplitude a0 (through the linear initialiser).
 """
@@ -145,6 +147,48 @@ def test_checkpoint_interval_does_not_change_gradient():
         assert abs(g[0] - ref[0]) <= 1e-14 * abs(ref[0])
         assert np.max(np.abs(g[1] - ref[1])) <= 1e-12 * np.max(np.abs(ref[1]))
         assert np.max(np.abs(g[2] - ref[2])) <= 1e-12 * np.max(np.abs(ref[2]))
+
+
+@pytest.mark.parametrize("ckpt", [20, 3, 7])
+def test_repeated_backward_gives_the_same_gradient(ckpt):
+    # a second backward of the same tape: with several segments the first one replayed
+    # the early segments over the final state, which the second brings back before it
+    # seeds the kinetic-energy cotangent
+    wl = _small_slab()
+    sim = PT.make_sim(wl)
+    sim.tape_forward(20, ckpt)
+    out = []
+    for _ in range(2):
+        dE0, dB0 = sim.tape_backward(1.0)
+        dP = sim.tape_particle_grad(0)
+        out.append((dE0.cpu().numpy(), dB0.cpu().numpy(), dP["ux"].cpu().numpy()))
+    sim.close()
+    for a in range(3):
+        ref = out[0][a]
+        assert np.max(np.abs(ref)) > 0.0
+        assert np.max(np.abs(out[1][a] - ref)) <= 1e-12 * np.max(np.abs(ref)), a
+
+
+def test_rebuilt_positions_follow_absorbing_exits():
+    # a hot plasma in a box absorbing along z: particles leave during the recorded
+    # segment, so the positions and active flags rebuilt between every 5th step of a
+    # one-segment tape must follow the forward's own moves, exits included; a tape
+    # with a checkpoint every step rebuilds nothing
+    wl = W.uniform_plasma(n=(8, 8, 16), ppc=2, vth=0.6, seed=57)
+    wl.bc, wl.absorb_cells, wl.absorb_sigma = (0, 0, 1), 3, 0.2
+    nsteps = 25
+    sim = PT.make_sim(wl)
+    sim.tape_forward(nsteps, nsteps)
+    left = sim.count()
+    sim.close()
+    assert 0 < left < wl.nparticles - 20, left
+    ref = _gpu_gradient(wl, nsteps, 1)
+    g = _gpu_gradient(wl, nsteps, nsteps)
+    assert abs(g[0] - ref[0]) <= 1e-14 * abs(ref[0])
+    for a in (1, 2):
+        assert np.max(np.abs(g[a] - ref[a])) <= 1e-12 * np.max(np.abs(ref[a]))
+    for k in ("x", "y", "z", "ux", "uy", "uz"):
+        assert np.max(np.abs(g[3][k] - ref[3][k])) <= 1e-12 * np.max(np.abs(ref[3][k])), k
 
 
 def test_tape_forward_matches_oracle_and_pic_step():
