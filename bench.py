@@ -356,6 +356,7 @@ def time_laser_ramp(torch, pic, W, total=500, adj=50, ck=50):
     forward it reverses and against plain steps of the same state: FP64
     pic_step steps (a context loaded with the state at step total - adj) and
     the mixed context's own steps."""
+    torch.cuda.empty_cache()  # blocks cached by the earlier legs: the tape needs most of the device
     t0 = time.perf_counter()
     wl = W.config("c5")
     gen_s = time.perf_counter() - t0
