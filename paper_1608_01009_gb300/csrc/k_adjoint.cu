@@ -337,7 +337,16 @@ __device__ void deposit_adjoint(const double* LJ, const GridDev& g, const int ce
 // periodic axes wrap, and the return value says whether the particle left an absorbing axis.
 // The tape's forward step and the rebuild of positions from a checkpoint (k_tape_move) both
 // call it; the products and sums are explicitly rounded (never contracted into an FMA), so a
-// rebuilt position equals the recorded one bit for bit.
+// rebuilt position equals the recorded one bit for bit.  The bounds are tested on the bit
+// patterns with integer compares, off the FP64 pipe that bounds both kernels.  As signed
+// integers the patterns of -0 .. -inf lie at or below that of -inf, and those of n .. +inf
+// between the patterns of n and +inf; a NaN falls in neither range, so like a floating-point
+// compare the tests leave it in place (and -0 counts as below 0, wrapping to +0).
+__device__ __forceinline__ bool below0(long long bx) { return bx <= (long long)0xFFF0000000000000ULL; }
+__device__ __forceinline__ bool at_or_above(long long bx, long long bn) {
+    return bx >= bn && bx <= 0x7FF0000000000000LL;
+}
+
 __device__ __forceinline__ bool move_of(const double xi[3], const double u[3], const StepParams& sp, double d[3],
                                         double x1[3]) {
     const double gi = rsqrt_ge1(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
@@ -345,11 +354,15 @@ __device__ __forceinline__ bool move_of(const double xi[3], const double u[3], c
     for (int c = 0; c < 3; ++c) {
         d[c] = __dmul_rn(u[c], __dmul_rn(gi, sp.dtd[c]));
         double x = __dadd_rn(xi[c], d[c]);
-        const double nc = (double)sp.g.n[c];
+        const long long bn = __double_as_longlong(sp.nd[c]);
+        long long bx = __double_as_longlong(x);
         if (sp.g.bc[c] == 0) {
-            if (x < 0.0) x = __dadd_rn(x, nc);
-            if (x >= nc) x = __dadd_rn(x, -nc);
-        } else if (x < 0.0 || x >= nc) {
+            if (below0(bx)) {
+                x = __dadd_rn(x, sp.nd[c]);
+                bx = __double_as_longlong(x);
+            }
+            if (at_or_above(bx, bn)) x = __dadd_rn(x, -sp.nd[c]);
+        } else if (below0(bx) || at_or_above(bx, bn)) {
             gone = true;
         }
         x1[c] = x;
