@@ -347,21 +347,27 @@ __device__ __forceinline__ bool at_or_above(long long bx, long long bn) {
     return bx >= bn && bx <= 0x7FF0000000000000LL;
 }
 
-__device__ __forceinline__ bool move_of(const double xi[3], const double u[3], const StepParams& sp, double d[3],
-                                        double x1[3]) {
+// The grid's cells per axis as doubles (the position bounds), formed on the host.
+struct Ext3 {
+    double n[3];
+};
+static Ext3 ext_of(const StepParams& sp) { return Ext3{{(double)sp.g.n[0], (double)sp.g.n[1], (double)sp.g.n[2]}}; }
+
+__device__ __forceinline__ bool move_of(const double xi[3], const double u[3], const StepParams& sp, const Ext3& ext,
+                                        double d[3], double x1[3]) {
     const double gi = rsqrt_ge1(fma(u[0], u[0], fma(u[1], u[1], fma(u[2], u[2], 1.0))));
     bool gone = false;
     for (int c = 0; c < 3; ++c) {
         d[c] = __dmul_rn(u[c], __dmul_rn(gi, sp.dtd[c]));
         double x = __dadd_rn(xi[c], d[c]);
-        const long long bn = __double_as_longlong(sp.nd[c]);
+        const long long bn = __double_as_longlong(ext.n[c]);
         long long bx = __double_as_longlong(x);
         if (sp.g.bc[c] == 0) {
             if (below0(bx)) {
-                x = __dadd_rn(x, sp.nd[c]);
+                x = __dadd_rn(x, ext.n[c]);
                 bx = __double_as_longlong(x);
             }
-            if (at_or_above(bx, bn)) x = __dadd_rn(x, -sp.nd[c]);
+            if (at_or_above(bx, bn)) x = __dadd_rn(x, -ext.n[c]);
         } else if (below0(bx) || at_or_above(bx, bn)) {
             gone = true;
         }
@@ -371,8 +377,8 @@ __device__ __forceinline__ bool move_of(const double xi[3], const double u[3], c
 }
 
 // One forward step of every particle.
-__global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, StepParams sp, const double* __restrict__ EB,
-                                                      double* __restrict__ J) {
+__global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, StepParams sp, Ext3 ext,
+                                                      const double* __restrict__ EB, double* __restrict__ J) {
     bool ok;
     const long long p = lane_strided(n, ok);
     if (!ok || !T.act[p]) return;
@@ -394,7 +400,7 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, S
         boris_fwd(u0, F, F + 3, sp.qdt2m, u, bf);
     }
     double d[3], x1[3];
-    const bool gone = move_of(xi, u, sp, d, x1);
+    const bool gone = move_of(xi, u, sp, ext, d, x1);
     const double w = T.w[p];
     if (w != 0.0 && sp.cq[0] != 0.0) {
         const double Q[3] = {sp.cq[0] * w, sp.cq[1] * w, sp.cq[2] * w};
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_step(TapeDev T, long long n, S
 // Rebuild of the next position from a recorded state: src holds x^n and its active flag,
 // with src.u = u^{n+1/2} (the momentum after the step); dst.xi and dst.act receive x^{n+1} and
 // its flag, exactly as k_tape_step moves the particle (dst may alias src; dst.u is unused).
-__global__ void __launch_bounds__(TAPE_NT) k_tape_move(TapeDev src, TapeDev dst, long long n, StepParams sp) {
+__global__ void __launch_bounds__(TAPE_NT) k_tape_move(TapeDev src, TapeDev dst, long long n, StepParams sp, Ext3 ext) {
     const long long p = (long long)blockIdx.x * TAPE_NT + threadIdx.x;
     if (p >= n) return;
     const double xi[3] = {src.xi[0][p], src.xi[1][p], src.xi[2][p]};
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_move(TapeDev src, TapeDev dst,
     }
     const double u[3] = {src.u[0][p], src.u[1][p], src.u[2][p]};
     double d[3], x1[3];
-    const bool gone = move_of(xi, u, sp, d, x1);
+    const bool gone = move_of(xi, u, sp, ext, d, x1);
     for (int c = 0; c < 3; ++c) dst.xi[c][p] = x1[c];
     dst.act[p] = gone ? 0 : 1;
 }
@@ -448,9 +454,9 @@ __global__ void __launch_bounds__(TAPE_NT) k_tape_seed(TapeDev T, LamDev L, long
 #ifndef PICGB_TAPE_MINB
 #define PICGB_TAPE_MINB 2  // CTAs per SM the adjoint kernel's register budget is set for
 #endif
-__global__ void __launch_bounds__(TAPE_NT, PICGB_TAPE_MINB) k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp,
-                                                         const double* __restrict__ EB, const double* __restrict__ LJ,
-                                                         double* __restrict__ scat) {
+__global__ void __launch_bounds__(TAPE_NT, PICGB_TAPE_MINB)
+    k_tape_adjoint(TapeDev T, LamDev L, long long n, StepParams sp, Ext3 ext, const double* __restrict__ EB,
+                   const double* __restrict__ LJ, double* __restrict__ scat) {
     bool ok;
     const long long p = lane_strided(n, ok);
     if (!ok || !T.act[p]) return;  // inactive: the step is the identity
@@ -484,7 +490,7 @@ __global__ void __launch_bounds__(TAPE_NT, PICGB_TAPE_MINB) k_tape_adjoint(TapeD
     double d[3];
     {
         double x1[3];
-        move_of(xi, u1, sp, d, x1);  // the forward's displacement, bit for bit
+        move_of(xi, u1, sp, ext, d, x1);  // the forward's displacement, bit for bit
     }
     // cotangents of the outputs
     double lx1[3] = {L.xi[0][p], L.xi[1][p], L.xi[2][p]};
@@ -762,12 +768,12 @@ static int pgrid(long long n) { return (int)((n + TAPE_NT - 1) / TAPE_NT); }
 
 cudaError_t tape_step_launch(cudaStream_t st, const TapeDev& T, long long n, const StepParams& sp, const double* EB,
                              double* J) {
-    if (n > 0) k_tape_step<<<pgrid(n), TAPE_NT, 0, st>>>(T, n, sp, EB, J);
+    if (n > 0) k_tape_step<<<pgrid(n), TAPE_NT, 0, st>>>(T, n, sp, ext_of(sp), EB, J);
     return cudaGetLastError();
 }
 
 cudaError_t tape_move_launch(cudaStream_t st, const TapeDev& src, const TapeDev& dst, long long n, const StepParams& sp) {
-    if (n > 0) k_tape_move<<<pgrid(n), TAPE_NT, 0, st>>>(src, dst, n, sp);
+    if (n > 0) k_tape_move<<<pgrid(n), TAPE_NT, 0, st>>>(src, dst, n, sp, ext_of(sp));
     return cudaGetLastError();
 }
 
@@ -779,7 +785,7 @@ cudaError_t tape_seed_launch(cudaStream_t st, const TapeDev& T, const LamDev& L,
 
 cudaError_t tape_adjoint_launch(cudaStream_t st, const TapeDev& T, const LamDev& L, long long n, const StepParams& sp,
                                 const double* EB, const double* LJ, double* scat) {
-    if (n > 0) k_tape_adjoint<<<pgrid(n), TAPE_NT, 0, st>>>(T, L, n, sp, EB, LJ, scat);
+    if (n > 0) k_tape_adjoint<<<pgrid(n), TAPE_NT, 0, st>>>(T, L, n, sp, ext_of(sp), EB, LJ, scat);
     return cudaGetLastError();
 }
 

@@ -870,7 +870,6 @@ StepParams step_params(const pic_ctx* c, const Species& s) {
     for (int a = 0; a < 3; ++a) {
         sp.dtd[a] = c->g.dt / c->g.d[a];
         sp.cq[a] = s.q / (c->g.dt * c->g.d[(a + 1) % 3] * c->g.d[(a + 2) % 3]);
-        sp.nd[a] = (double)c->g.n[a];
     }
     sp.mass = s.m;
     return sp;

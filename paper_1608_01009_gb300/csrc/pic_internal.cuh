@@ -158,7 +158,6 @@ struct LamDev {
 struct StepParams {
     GridDev g;
     double qdt2m, dtd[3], cq[3], mass;
-    double nd[3];  // the grid's cells per axis, as doubles (the position bounds)
 };
 
 #ifndef PICGB_CHUNK
